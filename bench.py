@@ -1,0 +1,375 @@
+"""Benchmark: staggered-grid Fourier pseudo-spectral elastic solver on GB300.
+
+Workload (default): 256^3 synthetic marine model (water column over five
+sediment layers, cp 1800-4000 m/s with depth gradient, cs = cp/1.8, Gardner
+rho, 5% Gaussian-correlated perturbation of correlation length 8 cells,
+seed 1), 12-cell PML, one random strike/dip/rake double couple in the
+reservoir box a third of the way down (seed 2), Ricker 30 Hz, dt from
+CFL 0.3, 3000 time steps, 64 x 64 seabed 4C receivers; every step of the
+benchmark also superposes 300 log-normal-amplitude events (origin times
+uniform in 2 s) of the step's traces into a 4C gather.
+
+One benchmark step = one es_run of all 3000 time steps (three velocity and
+three stress FFT-derivative passes, injection and recording per time step)
+plus the superposition.  value = nx ny nz nt / device time (Mcell-steps/s),
+summed over ranks.  Inputs (fields, materials: ~1.3 GB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the paper ships no code of its own).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1705_04874_gb300 import synth  # noqa: E402
+
+# algorithmic bytes per cell for one launch of each pass kernel (FP32):
+# velocity pass: 3 jobs x (read source + read/write target + read buoyancy)
+# stress pass: normal job (read v, r/w sxx syy szz, read lambda mu) + 2 shear
+# jobs (read v, r/w target, read edge mu); plus the PML slab splits, r/w, for
+# the fraction (2L+1)/n of the cells that hold them.
+VEL_BYTES_CELL = 3 * (4 + 8 + 4)
+STR_BYTES_CELL = (4 + 24 + 8) + 2 * (4 + 8 + 4)
+VEL_SLAB_TARGETS, STR_SLAB_TARGETS = 3, 5
+
+
+def workload(name):
+    if name == "256":
+        return dict(n=256, pml=12, nt=3000, rx=64, f0=30.0, seed=1, src_seed=2,
+                    desc="256^3 marine, PML 12, random DC in reservoir box, Ricker 30 Hz, "
+                         "3000 steps, 64x64 seabed 4C receivers, + superpose 300 events")
+    if name == "128":
+        return dict(n=128, pml=10, nt=2000, rx=32, f0=30.0, seed=1, src_seed=2,
+                    desc="128^3 marine, PML 10, DC strike 30 dip 60 rake 90, Ricker 30 Hz, "
+                         "2000 steps, 32x32 seabed 4C receivers, + superpose 300 events")
+    raise ValueError(name)
+
+
+def build_inputs(w, rank=0):
+    n = w["n"]
+    rho, cp, cs = synth.marine_model(n, seed=w["seed"])
+    dt = 0.3 * 10.0 / float(cp.max())  # CFL 0.3 (Eq. (5))
+    box = synth.reservoir_box((n, n, n), w["pml"])
+    rng = synth.SplitMix64(w["src_seed"] + 1000 * rank)
+    if n == 128:
+        mt = synth.double_couple_sdr(30, 60, 90)
+        pos = tuple((lo + hi) // 2 for lo, hi in box)
+    else:
+        mt = synth.random_dc(rng)
+        pos = tuple(int(v) for v in synth.random_positions(rng, box, 1)[0]) if rank else \
+            tuple((lo + hi) // 2 for lo, hi in box)
+    wav = synth.ricker(w["nt"], dt, w["f0"])
+    ev = synth.events(synth.SplitMix64(3), 300, 1, t_span=2.0)
+    n_out = w["nt"] + int(np.ceil(2.0 / dt))
+    return dict(rho=rho, cp=cp, cs=cs, dt=dt, mt=mt, pos=pos, wav=wav, ev=ev, n_out=n_out)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(gpus):
+    if gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    dist.init_process_group("gloo")
+    return rank, world, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(w, inp, steps, nthreads=0):
+    """Time the FP64 oracle on `steps` time steps of the workload."""
+    import oracle
+    oracle.build()
+    n = w["n"]
+    t0 = time.perf_counter()
+    rcv = oracle.seabed_receivers(inp["cs"], w["pml"], w["rx"], w["rx"])
+    oracle.simulate(inp["rho"], inp["cp"], inp["cs"], dx=10.0, dt=inp["dt"], nt=steps, pml=w["pml"],
+                    sources=[dict(kind="moment", pos=inp["pos"], m=inp["mt"], w=inp["wav"][:steps])],
+                    receivers=rcv, nthreads=nthreads)
+    el = time.perf_counter() - t0
+    cores = nthreads or oracle.default_threads()
+    return n ** 3 * steps / el / 1e6, el, cores
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inp = build_inputs(w)
+    steps = 2
+    for _ in range(args.warmup):
+        oracle_sample(w, inp, 1)
+    vals, els = [], []
+    cores = 0
+    for _ in range(args.steps):
+        v, el, cores = oracle_sample(w, inp, steps)
+        vals.append(v)
+        els.append(el)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": "Mcell-steps/s", "value": value, "unit": "Mcell-steps/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(els)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "grid": [w["n"]] * 3, "sample": f"{steps} time steps per step"},
+            "cpu_baseline": {"value": value, "unit": "Mcell-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} time steps of the {w['n']}^3 workload per step"},
+            "e2e": {"value": value, "unit": "Mcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="256", choices=["256", "128"])
+    ap.add_argument("--nt", type=int, default=0, help="override time steps per es_run (diagnostics)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = workload(args.workload)
+    if args.nt:
+        w["nt"] = args.nt
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_1705_04874_gb300 import es
+
+    rank, world, dist = dist_setup(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    inp = build_inputs(w, rank)
+    n, nt = w["n"], w["nt"]
+    stream = torch.cuda.current_stream()
+
+    m = es.Model(inp["rho"], inp["cp"], inp["cs"], dx=10.0, pml=w["pml"], stream=stream)
+    rcv = torch.from_numpy(m.seabed_receivers(w["rx"], w["rx"])).cuda()
+    n_rcv = rcv.shape[0]
+    m.source_set(inp["pos"], inp["mt"], torch.from_numpy(inp["wav"]).cuda())
+    traces = torch.empty((1, 4, n_rcv, nt), device="cuda")
+    gather = torch.empty((4, n_rcv, inp["n_out"]), device="cuda")
+    ev_src, ev_amp, ev_t0 = (torch.from_numpy(a).cuda() for a in inp["ev"])
+
+    def step():
+        m.state_reset()
+        m.run(nt, inp["dt"], rcv, traces[0])
+        es.es_superpose(traces, ev_src, ev_amp, ev_t0, inp["dt"], inp["n_out"], gather=gather, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    kern = []
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        kern.append(m.last_step_kernel_ms())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    ms = max_over_ranks(dist, ms)
+    cells = float(n) ** 3 * nt
+    total_cells = sum_over_ranks(dist, cells)
+    value = total_cells / (ms * 1e-3) / 1e6
+
+    # per-kernel time of a time step (CUDA events around each launch of the
+    # last time step of every es_run in the timed region)
+    kern = np.array(kern)
+    kmean = kern.mean(axis=0)
+    names = list(es.KERNEL_NAMES[:len(kmean)])
+    L = w["pml"]
+    slab_frac = (2 * L + 1) / n
+    bytes_cell = {k: VEL_BYTES_CELL + slab_frac * VEL_SLAB_TARGETS * 8 for k in names if k.startswith("vel")}
+    bytes_cell.update({k: STR_BYTES_CELL + slab_frac * STR_SLAB_TARGETS * 8 for k in names if k.startswith("str")})
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    passes = {k: kmean[i] for i, k in enumerate(names) if k in bytes_cell}
+    dom = max(passes, key=passes.get)
+    achieved = bytes_cell[dom] * n ** 3 / (passes[dom] * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            t = json.load(open(prof)).get(f"{args.workload}:{dom}")
+            traffic = t
+        except (OSError, ValueError):
+            traffic = None
+    kernels = {k: {"ms": round(float(kmean[i]), 5),
+                   "GBps": round(bytes_cell[k] * n ** 3 / (kmean[i] * 1e-3) / 1e9, 1) if k in bytes_cell else None}
+               for i, k in enumerate(names)}
+    step_bytes = sum(bytes_cell[k] for k in bytes_cell) * float(n) ** 3 * nt
+    kps = m.kernels_per_step()
+    launches = args.steps * (kps * nt + 3)
+
+    line = {"metric": "Mcell-steps/s", "value": value, "unit": "Mcell-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "grid": [n] * 3, "time_steps": nt, "receivers": n_rcv,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (fields+materials ~%.1f GB)" % (17 * 4 * n ** 3 / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": peak_src,
+                         "bytes_per_cell": round(bytes_cell[dom], 2)},
+            "useful_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4),
+            "kernels": kernels, "gpu_launches": launches}
+    if clk:
+        line["clocks"] = clk
+
+    if not args.no_e2e and rank == 0:
+        line["e2e"] = e2e(es, w, inp, stream)
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        v, el, cores = oracle_sample(w, inp, 3)
+        line["cpu_baseline"] = {"value": v, "unit": "Mcell-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"3 time steps of the {n}^3 workload ({el:.1f} s)"}
+    m.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e(es, w, inp, stream):
+    """Same metric through the C ABI with host buffers: model creation from
+    host arrays, source from host memory, traces and gather back to host
+    memory, every step (host<->device copies inside the timed region)."""
+    import torch
+    n, nt = w["n"], w["nt"]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    rho, cp, cs = pin(inp["rho"]), pin(inp["cp"]), pin(inp["cs"])
+    wav = pin(inp["wav"])
+    ev = [pin(a) for a in inp["ev"]]
+    host_tr = None
+    rcv_host = None
+
+    def step():
+        nonlocal host_tr, rcv_host
+        m = es.Model(rho, cp, cs, dx=10.0, pml=w["pml"], stream=stream)
+        if rcv_host is None:
+            rcv_host = pin(m.seabed_receivers(w["rx"], w["rx"]))
+            host_tr = torch.empty((1, 4, rcv_host.shape[0], nt)).pin_memory()
+        m.source_set(inp["pos"], inp["mt"], wav)
+        m.run(nt, inp["dt"], rcv_host, host_tr[0])
+        g = es.es_superpose(host_tr, ev[0], ev[1], ev[2], inp["dt"], inp["n_out"], stream=stream)
+        m.close()
+        return g
+
+    step()
+    torch.cuda.synchronize()
+    reps = 2
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g = step()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / reps
+    n_rcv = rcv_host.shape[0]
+    h2d = 3 * 4 * n ** 3 + 4 * nt + 12 * n_rcv + host_tr.numel() * 4 + 300 * 12
+    d2h = host_tr.numel() * 4 + g.size * 4
+    return {"value": float(n) ** 3 * nt / el / 1e6, "unit": "Mcell-steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * el}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * es.h -- C ABI of libes.so, a GB300 (sm_103a) solver for the 3D heterogeneous
+ * elastic wave equation by the staggered-grid Fourier pseudo-spectral method,
+ * recording 4C seabed seismograms, after Das, Chen & Hobson, arXiv 1705.04874.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Grids are [nz][ny][nx] FP32 arrays, x fastest, z = 0 at the sea surface
+ *   and increasing with depth.  Linear index = ix + nx * (iy + ny * iz).
+ * - Staggering (velocity at half time steps, stress at whole steps):
+ *   sxx, syy, szz at (i, j, k); vx at (i+1/2, j, k); vy at (i, j+1/2, k);
+ *   vz at (i, j, k+1/2); sxy at (i+1/2, j+1/2, k); sxz at (i+1/2, j, k+1/2);
+ *   syz at (i, j+1/2, k+1/2).  Every field is stored at the index of its
+ *   lower corner.
+ * - Pointer arguments may be host or device memory unless stated otherwise;
+ *   the library detects the kind with cudaPointerGetAttributes.  Inputs are
+ *   copied (the caller keeps ownership); outputs are caller-owned buffers.
+ * - Every call returns ES_OK or a negative status and writes no output on
+ *   error.  Work is ordered on the model's stream (default: the legacy
+ *   default stream); a call that returns ES_OK into a host buffer has
+ *   finished; into a device buffer, it is complete in stream order.
+ * - A model is not thread-safe: one thread at a time per model.
+ * - Axis lengths must factor as R1 * R2 with R1, R2 in {3,4,5,6,8,10,12,16}
+ *   in the supported list (16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192,
+ *   256); nx must be one of them too.  Anything else is ES_ERR_SIZE.
+ */
+#ifndef ES_H
+#define ES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct es_model es_model; /* opaque, library-owned */
+
+enum {
+    ES_OK = 0,
+    ES_ERR_ARG = -1,      /* bad argument (null, out of range, source in PML, ...) */
+    ES_ERR_SIZE = -2,     /* unsupported grid axis length */
+    ES_ERR_CUDA = -3,     /* a CUDA call failed (the message is kept, see es_last_error) */
+    ES_ERR_OOM = -4,      /* device allocation failed */
+    ES_ERR_UNSTABLE = -5, /* time step beyond the stability limit, or a non-finite field */
+    ES_ERR_TIMEOUT = -6,  /* a bounded device wait ran out */
+    ES_ERR_STATE = -7     /* call not valid in the model's current state */
+};
+
+/* Builds a model from density rho [kg/m^3], P velocity cp and S velocity cs
+ * [m/s] per grid point (Sec. II-A, Eq. (4): mu = cs^2 rho, lambda + 2 mu =
+ * cp^2 rho; water has cs = 0), grid spacing dx [m] on all axes and a PML of
+ * `pml` cells inside the grid at every face (Sec. II-B, 10 in the paper).
+ * Material parameters, staggered buoyancies (2 / (rho_a + rho_b)) and edge
+ * shear moduli (harmonic mean of the 4 surrounding mu, 0 next to water) are
+ * computed once in FP64 and stored in FP32; neighbours wrap at the last
+ * index.  Requires cs <= cp / sqrt(2) (lambda >= 0), rho > 0, cp > 0,
+ * 0 <= pml and 2 * pml + 2 < every axis length.  *out receives the model.
+ * Allocates ~ (17 + 24 (2 pml + 1) / n) nx ny nz floats of device memory. */
+int es_model_create(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz,
+                    double dx, int pml, es_model** out);
+
+/* Anisotropic spacing [m] (the paper's grid is 12.5 / 12.5 / 10 m, Sec. II-B). */
+int es_model_set_spacing(es_model* m, double dx, double dy, double dz);
+
+/* PML strength: alpha(xi) = alpha0 (cref / d) xi^4, factor exp(-alpha dt / 2)
+ * before and after each split increment.  Defaults alpha0 = 2, cref = max cp
+ * (cref <= 0 selects max cp). */
+int es_model_set_pml(es_model* m, double alpha0, double cref);
+
+/* Stream for all work of this model: a cudaStream_t passed as void*
+ * (e.g. torch.cuda.current_stream().cuda_stream).  NULL = legacy default. */
+int es_model_set_stream(es_model* m, void* stream);
+
+/* Default time step from the CFL rule (Sec. II-B, Eq. (5), CFL 0.3):
+ * dt = 0.3 min(dx, dy, dz) / max cp. */
+int es_model_default_dt(const es_model* m, double* dt);
+
+/* Replaces all sources by one moment-tensor point source (Sec. II-A point
+ * sources; Sec. V, Eq. (6)-(7) mechanisms, read as a symmetric tensor).
+ * pos = (ix, iy, iz) grid cell, each in [pml, n - 2 - pml] (outside the PML).
+ * mt = (Mxx, Myy, Mzz, Mxy, Mxz, Myz) [Pa]; after the stress half of step n
+ * every stress component at the source index gains M_ij * wavelet[n]
+ * (wavelet[n] = 0 for n >= nw).  wavelet: nw floats, host or device. */
+int es_source_set(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw);
+
+/* Adds a further moment-tensor source (same meaning as es_source_set). */
+int es_source_add(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw);
+
+/* Adds a point force f = (fx, fy, fz) [N]: after the velocity half of step n,
+ * v_i at the source index gains dt f_i wavelet[n] / (rho_i dx dy dz), rho_i
+ * the density at v_i's staggered point. */
+int es_source_add_force(es_model* m, const int pos[3], const double f[3], const float* wavelet,
+                        int nw);
+
+/* Removes every source. */
+int es_source_clear(es_model* m);
+
+/* Sets every field to zero (the state before the first step). */
+int es_state_reset(es_model* m);
+
+/* Field state as 9 [nz][ny][nx] FP32 arrays in the order vx vy vz sxx syy
+ * szz sxy sxz syz (velocity at t - dt/2, stress at t).  es_state_set puts
+ * each value on the field's x split (y split for syz) inside the PML. */
+int es_state_get(es_model* m, float* fields);
+int es_state_set(es_model* m, const float* fields);
+
+/* Runs nt time steps of the leapfrog scheme (Sec. II-A) from the model's
+ * current state and records 4C traces (Sec. II-A, Eq. (3)):
+ *   traces[0][r][n] = p = -(sxx + syy + szz) / 3 at t_{n+1}
+ *   traces[1..3][r][n] = vx, vy, vz at t_{n+1/2}
+ * at receiver r = (ix, iy, iz) of rcv [n_rcv][3] (each component at its own
+ * staggered point, no interpolation).  dt <= 0 selects es_model_default_dt.
+ * Returns ES_ERR_UNSTABLE if c_max dt sqrt(1/dx^2 + 1/dy^2 + 1/dz^2) > 2/pi
+ * or if a field became non-finite.  traces: [4][n_rcv][nt] floats, host or
+ * device; n_rcv may be 0 (traces then unused).  The state carries over to
+ * the next call (call es_state_reset for a fresh run). */
+int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces);
+
+/* Superposition of single-event traces (Sec. IV): for every event e,
+ * k_e = floor(t0s[e] / dt + 1/2) (computed in FP64) and
+ *   gather[c][r][t] = sum_e amps[e] * traces[src_of_event[e]][c][r][t - k_e],
+ * terms with t - k_e outside [0, nt) being zero (zero padding; negative t0
+ * cuts the front).  traces: [n_src][4][n_rcv][nt]; gather: [4][n_rcv][n_out].
+ * All arrays host or device; stream as in es_model_set_stream.  FP32 sums in
+ * event order. */
+int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* src_of_event,
+                 const float* amps, const float* t0s, int n_events, double dt, int n_out,
+                 float* gather, void* stream);
+
+/* Seabed receiver grid (Sec. II-B, Fig. 2): rx * ry receivers over the
+ * non-PML interior, ix_i = pml + ((2i+1)(nx - 2 pml)) / (2 rx) (integer
+ * division), likewise in y; iz = the last cell of the top run of cs == 0 in
+ * that column.  rcv: [rx*ry][3] ints, host memory, r = i + rx * j.
+ * ES_ERR_ARG if a chosen column has cs != 0 at the surface. */
+int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv);
+
+/* One staggered spectral derivative (Sec. II-A): out = D_axis^(shift) f,
+ * D(+/-) f (x) = f'(x +/- d/2), i.e. forward FFT along the axis, multiply by
+ * i kappa exp(+/- i kappa d / 2), inverse FFT, with kappa_m = 2 pi m / (n d),
+ * m = -n/2 .. n/2 - 1.  The same fused FFT pass kernels as es_run.  f, out:
+ * [nz][ny][nx] device pointers (distinct); shift = +1 or -1. */
+int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out,
+                  void* stream);
+
+/* Device time [ms] of each kernel of the last time step of the last es_run
+ * (CUDA events around each kernel launch of that step), in launch order:
+ * vel-x, vel-y, vel-z, str-x, str-y, str-z, inject, record.  n = capacity;
+ * returns the number written (>= 0) or a negative status. */
+int es_last_step_kernel_ms(es_model* m, float* ms, int n);
+
+/* Number of kernel launches one time step makes (for launch accounting). */
+int es_kernels_per_step(const es_model* m);
+
+void es_model_destroy(es_model* m);
+
+/* Static description of a status code. */
+const char* es_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* es_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ES_H */

@@ -97,12 +97,15 @@ static void fft_rec(const double complex *x, int stride, double complex *y, int 
     /* X[k + m s] = sum_q W_n^(q (k + m s)) Y_q[k] */
     for (int k = 0; k < m; ++k)
         for (int s = 0; s < p; ++s) {
-            double complex acc = 0.0;
-            for (int q = 0; q < p; ++q) {
-                long e = ((long)q * (long)(k + m * s)) % n;
-                acc += w_top[e * wstep] * y[(size_t)q * m + k];
+            const int step = k + m * s; /* < n */
+            double complex acc = y[k];  /* q = 0: W^0 = 1 */
+            int e = 0;                  /* e = q * step mod n */
+            for (int q = 1; q < p; ++q) {
+                e += step;
+                if (e >= n) e -= n;
+                acc += w_top[(size_t)e * wstep] * y[(size_t)q * m + k];
             }
-            tmp[k + m * s] = acc;
+            tmp[step] = acc;
         }
     memcpy(y, tmp, sizeof(double complex) * (size_t)n);
 }
@@ -341,6 +344,12 @@ int orc_pml_profile(int n, int L, double alpha0, double cref, double d, double d
 
 enum { VX, VY, VZ, SXX, SYY, SZZ, SXY, SXZ, SYZ, NF };
 
+/* Cell loops run in parallel over z planes; every cell is independent, so
+ * the arithmetic is the same as a serial loop. */
+#define OMP_PRAGMA(x) _Pragma(#x)
+#define OMP_CELLS OMP_PRAGMA(omp parallel for schedule(static) num_threads(nthr))
+#define OMP_TOTAL OMP_PRAGMA(omp parallel for schedule(static) num_threads(nthr))
+
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz;
@@ -438,6 +447,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
     double dxyz[3] = {p->dx, p->dy, p->dz};
     int dims[3] = {nx, ny, nz};
     double dt = p->dt;
+    int nthr = p->nthreads > 0 ? p->nthreads : 1;
 
     double *lam = malloc(sizeof(double) * ncell), *mu = malloc(sizeof(double) * ncell);
     double *b[3], *mue[3];
@@ -475,7 +485,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
     double *vold[3] = {NULL, NULL, NULL};
     if (energy_out) for (int c = 0; c < 3; ++c) vold[c] = malloc(sizeof(double) * ncell);
 
-#define TOTAL(f) do { for (size_t q = 0; q < ncell; ++q) { double s_ = 0.0; \
+#define TOTAL(f) do { OMP_TOTAL for (size_t q = 0; q < ncell; ++q) { double s_ = 0.0; \
         for (int a_ = 0; a_ < 3; ++a_) if (split[f][a_]) s_ += split[f][a_][q]; tot[f][q] = s_; } } while (0)
 
     for (int n = 0; n < nt; ++n) {
@@ -488,7 +498,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
             double *s = split[T->target][T->axis];
             const double *coef = b[T->target - VX];
             const double *P = stag_along(T->target, T->axis) ? Ps[T->axis] : Pc[T->axis];
-            for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
+            OMP_CELLS for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
                 size_t q = IDX(i, j, k);
                 int ia = T->axis == 0 ? i : (T->axis == 1 ? j : k);
                 s[q] = P[ia] * (P[ia] * s[q] + dt * coef[q] * D[q]);
@@ -518,7 +528,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
                 if (T->axis != a) continue;
                 double *s = split[T->target][a];
                 int diag = (T->target - SXX) == a;
-                for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
+                OMP_CELLS for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
                     size_t q = IDX(i, j, k);
                     int ia = a == 0 ? i : (a == 1 ? j : k);
                     double c = lam[q] + (diag ? 2.0 * mu[q] : 0.0);
@@ -531,7 +541,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
             orc_deriv(tot[T->source], nx, ny, nz, T->axis, dxyz[T->axis], T->shift, D, p->deriv_mode, p->nthreads);
             double *s = split[T->target][T->axis];
             const double *coef = mue[T->target - SXY];
-            for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
+            OMP_CELLS for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
                 size_t q = IDX(i, j, k);
                 int ia = T->axis == 0 ? i : (T->axis == 1 ? j : k);
                 s[q] = Ps[T->axis][ia] * (Ps[T->axis][ia] * s[q] + dt * coef[q] * D[q]);

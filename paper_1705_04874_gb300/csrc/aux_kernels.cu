@@ -1,0 +1,183 @@
+// Small kernels around the derivative passes: point-source injection
+// (Sec. II-A: point sources at grid points), 4C receiver recording
+// (Sec. II-A, Eq. (3); Sec. II-B), superposition of single-event traces
+// (Sec. IV), a non-finite scan and slab initialisation.
+#include "es_internal.h"
+
+namespace es {
+
+// One thread walks every source in order, so sources sharing a cell add in a
+// fixed order.  The step counter lives on the device so that one captured
+// step can be replayed: the kernel that runs last in a step (`advance`)
+// publishes the step index to `cur` for the recorder and increments it.
+__global__ void inject_kernel(float* const* fields, const SourceDev* src, int nsrc, int kind,
+                              int* counter, int* cur, int advance)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = *counter;
+    for (int e = 0; e < nsrc; ++e) {
+        const SourceDev s = src[e];
+        if (s.kind != kind || n >= s.nw) continue;
+        const float w = s.w[n];
+        if (kind == 0) {
+            // moment tensor: stress component i gains M_i w[n] (Mxx Myy Mzz Mxy Mxz Myz)
+            for (int c = 0; c < 6; ++c)
+                if (s.m[c] != 0.f) fields[SXX + c][s.cell] += s.m[c] * w;
+        } else {
+            // point force: m[c] = dt f_c / (rho_c dx dy dz), folded on the host
+            for (int c = 0; c < 3; ++c)
+                if (s.m[c] != 0.f) fields[VX + c][s.cell] += s.m[c] * w;
+        }
+    }
+    if (advance) {
+        *cur = n;
+        *counter = n + 1;
+    }
+}
+
+cudaError_t launch_inject(float* const* fields, const SourceDev* src, int nsrc, int kind, int* counter,
+                          int* cur, int advance, cudaStream_t st)
+{
+    inject_kernel<<<1, 32, 0, st>>>(fields, src, nsrc, kind, counter, cur, advance);
+    return cudaGetLastError();
+}
+
+// rec[n - start][c][r]: sample n of component c (p, vx, vy, vz) at receiver r
+__global__ void record_kernel(float* const* fields, const long long* rcv_cell, int n_rcv, const int* cur,
+                              long long start, float* rec)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rcv) return;
+    const long long q = rcv_cell[r];
+    const size_t row = (size_t)(*cur - start) * 4 * n_rcv;
+    const float s = fields[SXX][q] + fields[SYY][q] + fields[SZZ][q];
+    rec[row + r] = -s / 3.f;  // Eq. (3)
+    rec[row + n_rcv + r] = fields[VX][q];
+    rec[row + 2 * (size_t)n_rcv + r] = fields[VY][q];
+    rec[row + 3 * (size_t)n_rcv + r] = fields[VZ][q];
+}
+
+cudaError_t launch_record(float* const* fields, const long long* rcv_cell, int n_rcv, const int* cur,
+                          long long start, float* rec, cudaStream_t st)
+{
+    if (n_rcv <= 0) return cudaSuccess;
+    record_kernel<<<(n_rcv + 127) / 128, 128, 0, st>>>(fields, rcv_cell, n_rcv, cur, start, rec);
+    return cudaGetLastError();
+}
+
+// [nt][4 n_rcv] -> [4 n_rcv][nt] through a 32 x 32 shared tile
+__global__ void transpose_kernel(const float* in, int rows, int cols, float* out)
+{
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose_traces(const float* rec, int nt, int n_rcv, float* out, cudaStream_t st)
+{
+    const int cols = 4 * n_rcv;
+    dim3 grid((cols + 31) / 32, (nt + 31) / 32), block(32, 8);
+    transpose_kernel<<<grid, block, 0, st>>>(rec, nt, cols, out);
+    return cudaGetLastError();
+}
+
+// gather[row][t] = sum_e amp_e traces[src_e][row][t - k_e], rows = 4 n_rcv.
+// One thread per output sample; events in order (FP32 accumulation).
+__global__ void superpose_kernel(const float* traces, int n_rcv, int nt, const int* ev_src,
+                                 const float* ev_amp, const int* ev_shift, int n_events, int n_out,
+                                 float* gather)
+{
+    extern __shared__ int s_ev[];
+    int* s_src = s_ev;
+    int* s_k = s_ev + n_events;
+    float* s_a = reinterpret_cast<float*>(s_ev + 2 * n_events);
+    for (int i = threadIdx.x; i < n_events; i += blockDim.x) {
+        s_src[i] = ev_src[i];
+        s_k[i] = ev_shift[i];
+        s_a[i] = ev_amp[i];
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t row = blockIdx.y;
+    if (t >= n_out) return;
+    const size_t rows = 4 * (size_t)n_rcv;
+    float acc = 0.f;
+    for (int e = 0; e < n_events; ++e) {
+        const long u = (long)t - s_k[e];
+        if (u < 0 || u >= nt) continue;
+        acc += s_a[e] * __ldg(traces + ((size_t)s_src[e] * rows + row) * nt + u);
+    }
+    gather[row * n_out + t] = acc;
+}
+
+cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* ev_src,
+                             const float* ev_amp, const int* ev_shift, int n_events, int n_out, float* gather,
+                             cudaStream_t st)
+{
+    (void)n_src;
+    dim3 grid((n_out + 255) / 256, 4 * n_rcv);
+    const size_t sm = (size_t)n_events * 3 * sizeof(int);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(superpose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    superpose_kernel<<<grid, 256, sm, st>>>(traces, n_rcv, nt, ev_src, ev_amp, ev_shift, n_events, n_out, gather);
+    return cudaGetLastError();
+}
+
+// flag |= 1 if any field value is NaN or infinite
+__global__ void nonfinite_kernel(float* const* fields, size_t n, int* flag)
+{
+    int bad = 0;
+    for (int f = 0; f < NFIELD; ++f) {
+        const float* a = fields[f];
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+            bad |= !isfinite(a[i]);
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_nonfinite(float* const* fields, size_t n, int* flag, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    nonfinite_kernel<<<sms * 4, 256, 0, st>>>(fields, n, flag);
+    return cudaGetLastError();
+}
+
+// slab[cell in slab] = copy ? total[cell] : 0
+__global__ void fill_slab_kernel(const float* total, float* slab, int axis, int nx, int ny, int nz, int L,
+                                 int copy)
+{
+    const int S = 2 * L + 1;
+    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const size_t cnt = (size_t)nx * ny * nz / n * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt; i += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z, sp;
+        if (axis == 0) { sp = (int)(i % S); size_t l = i / S; y = (int)(l % ny); z = (int)(l / ny); x = 0; }
+        else if (axis == 1) { x = (int)(i % nx); size_t l = i / nx; sp = (int)(l % S); z = (int)(l / S); y = 0; }
+        else { x = (int)(i % nx); size_t l = i / nx; y = (int)(l % ny); sp = (int)(l / ny); z = 0; }
+        const int pos = sp < L ? sp : sp - L + (n - 1 - L);
+        if (axis == 0) x = pos; else if (axis == 1) y = pos; else z = pos;
+        slab[i] = copy ? total[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)] : 0.f;
+    }
+}
+
+cudaError_t launch_fill_slab(const float* total, float* slab, int axis, int nx, int ny, int nz, int L, int copy,
+                             cudaStream_t st)
+{
+    fill_slab_kernel<<<1024, 256, 0, st>>>(total, slab, axis, nx, ny, nz, L, copy);
+    return cudaGetLastError();
+}
+
+}  // namespace es

@@ -1,0 +1,864 @@
+// Host side of libes.so: the C ABI declared in include/es.h.
+//
+// A model owns, in one device allocation, the nine field totals (vx vy vz
+// sxx syy szz sxy sxz syz), eight FP32 material arrays and, for each axis,
+// the split part of every field driven by that axis's derivatives -- but only
+// inside that axis's PML slabs ([0, L) and [n-1-L, n)), the only cells where a
+// split evolves differently from the total (Sec. II-B split-field PML).
+// A time step (Sec. II-A leapfrog) is 3 velocity passes + 3 stress passes
+// (fft_pass.cuh), point-source injection and 4C recording; es_run captures it
+// as a CUDA graph and replays it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/es.h"
+#include "es_internal.h"
+
+using namespace es;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ES_ERR_OOM : ES_ERR_CUDA;
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
+    } while (0)
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy n elements of T from host or device memory into a host vector
+template <class T>
+int fetch(const T* src, size_t n, std::vector<T>& out, cudaStream_t st)
+{
+    out.resize(n);
+    if (n == 0) return ES_OK;
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(out.data(), src, n * sizeof(T));
+    }
+    return ES_OK;
+}
+
+int g_prepared_dev = -1;
+
+int ensure_prepared()
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (g_prepared_dev != dev) {
+        CK(prepare_pass_kernels());
+        g_prepared_dev = dev;
+    }
+    return ES_OK;
+}
+
+bool axis_ok(int n) { int a, b; return plan_radices(n, &a, &b) != 0; }
+
+// i kappa exp(sign i kappa d / 2) / n and exp(-2 pi i m / n), in FP64 then rounded
+void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& hp, std::vector<float2>& hm)
+{
+    const double pi = 3.14159265358979323846;
+    tw.resize(n);
+    hp.resize(n);
+    hm.resize(n);
+    for (int m = 0; m < n; ++m) {
+        const double a = 2.0 * pi * (double)m / (double)n;
+        tw[m] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+        const int mk = (2 * m < n) ? m : m - n;  // even n: bin n/2 -> -n/2
+        const double kap = 2.0 * pi * (double)mk / ((double)n * d);
+        for (int s = 0; s < 2; ++s) {
+            const double ph = (s == 0 ? 0.5 : -0.5) * kap * d;
+            const float2 h = make_float2((float)(-kap * std::sin(ph) / n), (float)(kap * std::cos(ph) / n));
+            (s == 0 ? hp : hm)[m] = h;
+        }
+    }
+}
+
+struct Src {
+    int kind;
+    int pos[3];
+    double m[6];
+    float* d_w;
+    int nw;
+};
+
+const int KPS_MAX = 9;  // kernels per step (8, +1 with force sources)
+
+}  // namespace
+
+struct es_model {
+    int nx, ny, nz;
+    size_t ncell;
+    double d[3];
+    int L;
+    double alpha0 = 2.0, cref = 0.0;
+    cudaStream_t stream = nullptr;
+    std::vector<float> rho, cs;  // host copies (seabed rule, force scaling)
+    float cp_max = 0.f;
+    char* pool = nullptr;
+    float* f[NFIELD] = {};
+    float* slab[3][NFIELD] = {};
+    float* mat[NMAT] = {};
+    float** d_fields = nullptr;
+    float2 *tw[3] = {}, *hp[3] = {}, *hm[3] = {};
+    float *pc[3] = {}, *ps[3] = {};
+    int* d_int = nullptr;  // [0] step counter, [1] current step, [2] non-finite flag
+    std::vector<Src> srcs;
+    SourceDev* d_src = nullptr;
+    int d_src_cap = 0;
+    float* d_rec = nullptr;
+    size_t rec_cap = 0;
+    float* d_out = nullptr;
+    size_t out_cap = 0;
+    long long* d_rcv = nullptr;
+    int rcv_cap = 0;
+    long long steps_done = 0;
+    cudaEvent_t ev[2 * KPS_MAX] = {};
+    float last_ms[KPS_MAX] = {};
+    int n_last = 0;
+};
+
+namespace {
+
+bool has_split(int f, int a)
+{
+    return !((f == SXY && a == 2) || (f == SXZ && a == 1) || (f == SYZ && a == 0));
+}
+bool stag_along(int f, int a)
+{
+    switch (f) {
+    case VX: return a == 0;
+    case VY: return a == 1;
+    case VZ: return a == 2;
+    case SXY: return a == 0 || a == 1;
+    case SXZ: return a == 0 || a == 2;
+    case SYZ: return a == 1 || a == 2;
+    default: return false;
+    }
+}
+int axis_len(const es_model* m, int a) { return a == 0 ? m->nx : (a == 1 ? m->ny : m->nz); }
+size_t slab_count(const es_model* m, int a) { return m->L > 0 ? m->ncell / axis_len(m, a) * (2 * m->L + 1) : 0; }
+
+int upload_sources(es_model* m, double dt)
+{
+    std::vector<SourceDev> h(m->srcs.size());
+    const double vol = m->d[0] * m->d[1] * m->d[2];
+    for (size_t e = 0; e < m->srcs.size(); ++e) {
+        const Src& s = m->srcs[e];
+        SourceDev& d = h[e];
+        d.kind = s.kind;
+        d.cell = (long long)s.pos[0] + (long long)m->nx * ((long long)s.pos[1] + (long long)m->ny * s.pos[2]);
+        d.w = s.d_w;
+        d.nw = s.nw;
+        for (int c = 0; c < 6; ++c) d.m[c] = 0.f;
+        if (s.kind == 0) {
+            for (int c = 0; c < 6; ++c) d.m[c] = (float)s.m[c];
+        } else {
+            // dt f_c / (rho at v_c's staggered point * dx dy dz)
+            for (int c = 0; c < 3; ++c) {
+                int p1[3] = {s.pos[0], s.pos[1], s.pos[2]};
+                p1[c] = (p1[c] + 1) % axis_len(m, c);
+                const size_t q0 = (size_t)d.cell;
+                const size_t q1 = (size_t)p1[0] + (size_t)m->nx * ((size_t)p1[1] + (size_t)m->ny * p1[2]);
+                const double b = 2.0 / ((double)m->rho[q0] + (double)m->rho[q1]);
+                d.m[c] = (float)(dt * s.m[c] * b / vol);
+            }
+        }
+    }
+    if ((int)h.size() > m->d_src_cap) {
+        cudaFree(m->d_src);
+        m->d_src = nullptr;
+        m->d_src_cap = 0;
+        CK(cudaMalloc(&m->d_src, sizeof(SourceDev) * h.size()));
+        m->d_src_cap = (int)h.size();
+    }
+    if (!h.empty()) {
+        CK(cudaMemcpyAsync(m->d_src, h.data(), sizeof(SourceDev) * h.size(), cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    return ES_OK;
+}
+
+PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
+{
+    PassParams p;
+    std::memset(&p, 0, sizeof p);
+    p.nx = m->nx;
+    p.ny = m->ny;
+    p.nz = m->nz;
+    p.axis = axis;
+    p.n = axis_len(m, axis);
+    p.njobs = 3;
+    p.tw = m->tw[axis];
+    p.hp = m->hp[axis];
+    p.hm = m->hm[axis];
+    p.pc = m->pc[axis];
+    p.ps = m->ps[axis];
+    p.L = m->L;
+    p.dt = dt;
+    auto single = [&](PassJob& J, int src, int sign, int tgt, int coef) {
+        J.src = m->f[src];
+        J.kind = JOB_SINGLE;
+        J.sign = sign;
+        J.tgt[0] = m->f[tgt];
+        J.slab[0] = m->slab[axis][tgt];
+        J.coef[0] = m->mat[coef];
+        J.stag = stag_along(tgt, axis);
+    };
+    if (!stress) {
+        // dv_i/dt = (1/rho) d sigma_ij / dx_j (Eq. (2)), term along `axis`
+        static const int src_tab[3][3] = {{SXX, SXY, SXZ}, {SXY, SYY, SYZ}, {SXZ, SYZ, SZZ}};
+        for (int i = 0; i < 3; ++i) {
+            const int src = src_tab[axis][i];
+            const int sign = (i == axis) ? +1 : -1;  // normal stress -> half index: +; shear -> whole: -
+            single(p.job[i], src, sign, VX + i, M_BX + i);
+        }
+    } else {
+        // d sigma_ij/dt = lambda delta_ij dv_k/dx_k + mu (dv_i/dx_j + dv_j/dx_i) (Eq. (2))
+        PassJob& J = p.job[0];
+        J.src = m->f[VX + axis];
+        J.kind = JOB_NORMAL;
+        J.sign = -1;
+        J.diag = axis;
+        for (int t = 0; t < 3; ++t) {
+            J.tgt[t] = m->f[SXX + t];
+            J.slab[t] = m->slab[axis][SXX + t];
+        }
+        J.coef[0] = m->mat[M_LAM];
+        J.coef[1] = m->mat[M_MU];
+        J.stag = 0;
+        // shear terms: d v_b / d x_axis feeds sigma_{axis b}
+        int k = 1;
+        for (int b = 0; b < 3; ++b) {
+            if (b == axis) continue;
+            const int lo = std::min(axis, b), hi = std::max(axis, b);
+            const int tgt = (lo == 0 && hi == 1) ? SXY : ((lo == 0 && hi == 2) ? SXZ : SYZ);
+            const int coef = (tgt == SXY) ? M_MUXY : ((tgt == SXZ) ? M_MUXZ : M_MUYZ);
+            single(p.job[k++], VX + b, +1, tgt, coef);
+        }
+    }
+    return p;
+}
+
+// Enqueues one time step; with `ev` non-null, events bracket every kernel.
+int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t st, cudaEvent_t* ev, int* nk)
+{
+    int k = 0;
+    // under stream capture only cudaEventRecordExternal makes a real record node
+    auto mark = [&](bool before) {
+        if (ev) cudaEventRecordWithFlags(ev[2 * k + (before ? 0 : 1)], st, cudaEventRecordExternal);
+    };
+    const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
+    for (int a = 0; a < 3; ++a) {
+        PassParams p = make_pass(m, a, false, dt);
+        mark(true);
+        CK(launch_pass(p, st));
+        mark(false);
+        ++k;
+    }
+    if (has_force) {
+        mark(true);
+        CK(launch_inject(m->d_fields, m->d_src, (int)m->srcs.size(), 1, m->d_int, m->d_int + 1, 0, st));
+        mark(false);
+        ++k;
+    }
+    for (int a = 0; a < 3; ++a) {
+        PassParams p = make_pass(m, a, true, dt);
+        mark(true);
+        CK(launch_pass(p, st));
+        mark(false);
+        ++k;
+    }
+    mark(true);
+    CK(launch_inject(m->d_fields, m->d_src, (int)m->srcs.size(), 0, m->d_int, m->d_int + 1, 1, st));
+    mark(false);
+    ++k;
+    if (n_rcv > 0) {
+        mark(true);
+        CK(launch_record(m->d_fields, m->d_rcv, n_rcv, m->d_int + 1, start, m->d_rec, st));
+        mark(false);
+        ++k;
+    }
+    *nk = k;
+    return ES_OK;
+}
+
+int capture(es_model* m, int steps, float dt, int n_rcv, long long start, bool timed, cudaGraphExec_t* exec)
+{
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    int rc = ES_OK, nk = 0;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    for (int s = 0; s < steps && rc == ES_OK; ++s) rc = enqueue_step(m, dt, n_rcv, start, cap, timed ? m->ev : nullptr, &nk);
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (rc != ES_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    m->n_last = nk;
+    return ES_OK;
+}
+
+int run_checked_args(es_model* m, int nt, double dt, int n_rcv)
+{
+    if (!m || nt < 0 || n_rcv < 0) return ES_ERR_ARG;
+    (void)dt;
+    return ES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* es_status_string(int s)
+{
+    switch (s) {
+    case ES_OK: return "ok";
+    case ES_ERR_ARG: return "invalid argument";
+    case ES_ERR_SIZE: return "unsupported grid size";
+    case ES_ERR_CUDA: return "CUDA error";
+    case ES_ERR_OOM: return "out of device memory";
+    case ES_ERR_UNSTABLE: return "unstable (time step too large or non-finite field)";
+    case ES_ERR_TIMEOUT: return "device wait timed out";
+    case ES_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+const char* es_last_error(void) { return g_err; }
+
+void es_model_destroy(es_model* m)
+{
+    if (!m) return;
+    for (auto& s : m->srcs) cudaFree(s.d_w);
+    cudaFree(m->d_src);
+    cudaFree(m->d_rec);
+    cudaFree(m->d_out);
+    cudaFree(m->d_rcv);
+    cudaFree(m->pool);
+    for (auto& e : m->ev)
+        if (e) cudaEventDestroy(e);
+    delete m;
+}
+
+int es_model_create(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz, double dx, int pml,
+                    es_model** out)
+{
+    if (!out) return ES_ERR_ARG;
+    *out = nullptr;
+    if (!rho || !cp || !cs || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || pml < 0) return ES_ERR_ARG;
+    if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return ES_ERR_SIZE;
+    if (2 * pml + 2 >= nx || 2 * pml + 2 >= ny || 2 * pml + 2 >= nz) return ES_ERR_ARG;
+    int rc = ensure_prepared();
+    if (rc != ES_OK) return rc;
+    const size_t n = (size_t)nx * ny * nz;
+    std::vector<float> h_rho, h_cp, h_cs;
+    if ((rc = fetch(rho, n, h_rho, nullptr)) != ES_OK) return rc;
+    if ((rc = fetch(cp, n, h_cp, nullptr)) != ES_OK) return rc;
+    if ((rc = fetch(cs, n, h_cs, nullptr)) != ES_OK) return rc;
+    float cpmax = 0.f;
+    for (size_t q = 0; q < n; ++q) {
+        const float r = h_rho[q], p = h_cp[q], s = h_cs[q];
+        if (!(r > 0.f) || !(p > 0.f) || !(s >= 0.f) || !std::isfinite(r) || !std::isfinite(p) || !std::isfinite(s))
+            return ES_ERR_ARG;
+        if ((double)p * p - 2.0 * (double)s * s < 0.0) return ES_ERR_ARG;  // lambda >= 0
+        cpmax = std::max(cpmax, p);
+    }
+    es_model* m = new (std::nothrow) es_model();
+    if (!m) return ES_ERR_OOM;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    m->ncell = n;
+    m->d[0] = m->d[1] = m->d[2] = dx;
+    m->L = pml;
+    m->cp_max = cpmax;
+    m->rho = h_rho;
+    m->cs = h_cs;
+
+    // one pool: fields, materials, slabs, per-axis tables, counters, pointer table
+    const size_t A = 256;
+    auto up = [&](size_t b) { return (b + A - 1) / A * A; };
+    size_t bytes = up(n * 4) * (NFIELD + NMAT);
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f)
+            if (pml > 0 && has_split(f, a)) bytes += up(slab_count(m, a) * 4);
+    for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 2 * up(axis_len(m, a) * 4);
+    bytes += up(16) + up(NFIELD * sizeof(float*));
+    cudaError_t e = cudaMalloc(&m->pool, bytes);
+    if (e != cudaSuccess) {
+        es_model_destroy(m);
+        return cuda_fail(e, "cudaMalloc(model)");
+    }
+    char* cur = m->pool;
+    auto take = [&](size_t b) { char* p = cur; cur += up(b); return p; };
+    for (int f = 0; f < NFIELD; ++f) m->f[f] = (float*)take(n * 4);
+    for (int k = 0; k < NMAT; ++k) m->mat[k] = (float*)take(n * 4);
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f)
+            m->slab[a][f] = (pml > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4) : nullptr;
+    for (int a = 0; a < 3; ++a) {
+        m->tw[a] = (float2*)take(axis_len(m, a) * 8);
+        m->hp[a] = (float2*)take(axis_len(m, a) * 8);
+        m->hm[a] = (float2*)take(axis_len(m, a) * 8);
+        m->pc[a] = (float*)take(axis_len(m, a) * 4);
+        m->ps[a] = (float*)take(axis_len(m, a) * 4);
+    }
+    m->d_int = (int*)take(16);
+    m->d_fields = (float**)take(NFIELD * sizeof(float*));
+
+    // materials in FP64 (Eq. (4) and the staggered averages), stored in FP32
+    {
+        std::vector<float> h(n);
+        auto idx = [&](int i, int j, int k) { return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k); };
+        std::vector<double> mu(n), lam(n);
+        for (size_t q = 0; q < n; ++q) {
+            mu[q] = (double)h_cs[q] * h_cs[q] * h_rho[q];
+            lam[q] = (double)h_cp[q] * h_cp[q] * h_rho[q] - 2.0 * mu[q];
+        }
+        auto hmean = [](double a, double b, double c, double d) {
+            return (a == 0.0 || b == 0.0 || c == 0.0 || d == 0.0) ? 0.0 : 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d);
+        };
+        for (int which = 0; which < NMAT && e == cudaSuccess; ++which) {
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        const size_t q = idx(i, j, k);
+                        const size_t qx = idx((i + 1) % nx, j, k), qy = idx(i, (j + 1) % ny, k), qz = idx(i, j, (k + 1) % nz);
+                        double v = 0.0;
+                        switch (which) {
+                        case M_BX: v = 2.0 / ((double)h_rho[q] + h_rho[qx]); break;
+                        case M_BY: v = 2.0 / ((double)h_rho[q] + h_rho[qy]); break;
+                        case M_BZ: v = 2.0 / ((double)h_rho[q] + h_rho[qz]); break;
+                        case M_LAM: v = lam[q]; break;
+                        case M_MU: v = mu[q]; break;
+                        case M_MUXY: v = hmean(mu[q], mu[qx], mu[qy], mu[idx((i + 1) % nx, (j + 1) % ny, k)]); break;
+                        case M_MUXZ: v = hmean(mu[q], mu[qx], mu[qz], mu[idx((i + 1) % nx, j, (k + 1) % nz)]); break;
+                        case M_MUYZ: v = hmean(mu[q], mu[qy], mu[qz], mu[idx(i, (j + 1) % ny, (k + 1) % nz)]); break;
+                        }
+                        h[q] = (float)v;
+                    }
+            e = cudaMemcpy(m->mat[which], h.data(), n * 4, cudaMemcpyHostToDevice);
+        }
+    }
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        std::vector<float2> tw, hp, hm;
+        axis_tables(axis_len(m, a), m->d[a], tw, hp, hm);
+        e = cudaMemcpy(m->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 2 * KPS_MAX && e == cudaSuccess; ++k) e = cudaEventCreate(&m->ev[k]);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(e, "es_model_create");
+        es_model_destroy(m);
+        return r;
+    }
+    rc = es_state_reset(m);
+    if (rc != ES_OK) {
+        es_model_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return ES_OK;
+}
+
+int es_model_set_spacing(es_model* m, double dx, double dy, double dz)
+{
+    if (!m || !(dx > 0) || !(dy > 0) || !(dz > 0)) return ES_ERR_ARG;
+    m->d[0] = dx;
+    m->d[1] = dy;
+    m->d[2] = dz;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<float2> tw, hp, hm;
+        axis_tables(axis_len(m, a), m->d[a], tw, hp, hm);
+        CK(cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice));
+    }
+    return ES_OK;
+}
+
+int es_model_set_pml(es_model* m, double alpha0, double cref)
+{
+    if (!m || !(alpha0 >= 0)) return ES_ERR_ARG;
+    m->alpha0 = alpha0;
+    m->cref = cref;
+    return ES_OK;
+}
+
+int es_model_set_stream(es_model* m, void* stream)
+{
+    if (!m) return ES_ERR_ARG;
+    m->stream = (cudaStream_t)stream;
+    return ES_OK;
+}
+
+int es_model_default_dt(const es_model* m, double* dt)
+{
+    if (!m || !dt) return ES_ERR_ARG;
+    *dt = 0.3 * std::min(m->d[0], std::min(m->d[1], m->d[2])) / (double)m->cp_max;  // Eq. (5), CFL 0.3
+    return ES_OK;
+}
+
+static int add_source(es_model* m, int kind, const int pos[3], const double* v, int nv, const float* w, int nw)
+{
+    if (!m || !pos || !v || nw < 0 || (nw > 0 && !w)) return ES_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (pos[a] < m->L || pos[a] > axis_len(m, a) - 2 - m->L) return ES_ERR_ARG;  // outside the PML slabs
+    for (int c = 0; c < nv; ++c)
+        if (!std::isfinite(v[c])) return ES_ERR_ARG;
+    std::vector<float> h;
+    int rc = fetch(w, (size_t)nw, h, m->stream);
+    if (rc != ES_OK) return rc;
+    Src s;
+    s.kind = kind;
+    std::memcpy(s.pos, pos, sizeof s.pos);
+    for (int c = 0; c < 6; ++c) s.m[c] = c < nv ? v[c] : 0.0;
+    s.nw = nw;
+    s.d_w = nullptr;
+    if (nw > 0) {
+        CK(cudaMalloc(&s.d_w, sizeof(float) * nw));
+        cudaError_t e = cudaMemcpy(s.d_w, h.data(), sizeof(float) * nw, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(s.d_w);
+            return cuda_fail(e, "cudaMemcpy(wavelet)");
+        }
+    }
+    m->srcs.push_back(s);
+    return ES_OK;
+}
+
+int es_source_clear(es_model* m)
+{
+    if (!m) return ES_ERR_ARG;
+    CK(cudaStreamSynchronize(m->stream));
+    for (auto& s : m->srcs) cudaFree(s.d_w);
+    m->srcs.clear();
+    return ES_OK;
+}
+
+int es_source_set(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw)
+{
+    if (!m) return ES_ERR_ARG;
+    int rc = es_source_clear(m);
+    if (rc != ES_OK) return rc;
+    return add_source(m, 0, pos, mt, 6, wavelet, nw);
+}
+
+int es_source_add(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw)
+{
+    return add_source(m, 0, pos, mt, 6, wavelet, nw);
+}
+
+int es_source_add_force(es_model* m, const int pos[3], const double f[3], const float* wavelet, int nw)
+{
+    return add_source(m, 1, pos, f, 3, wavelet, nw);
+}
+
+int es_state_reset(es_model* m)
+{
+    if (!m) return ES_ERR_ARG;
+    for (int f = 0; f < NFIELD; ++f) CK(cudaMemsetAsync(m->f[f], 0, m->ncell * 4, m->stream));
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f)
+            if (m->slab[a][f]) CK(cudaMemsetAsync(m->slab[a][f], 0, slab_count(m, a) * 4, m->stream));
+    CK(cudaMemsetAsync(m->d_int, 0, 16, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    m->steps_done = 0;
+    return ES_OK;
+}
+
+int es_state_get(es_model* m, float* fields)
+{
+    if (!m || !fields) return ES_ERR_ARG;
+    const cudaMemcpyKind k = is_device_ptr(fields) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int f = 0; f < NFIELD; ++f) CK(cudaMemcpyAsync(fields + (size_t)f * m->ncell, m->f[f], m->ncell * 4, k, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return ES_OK;
+}
+
+int es_state_set(es_model* m, const float* fields)
+{
+    if (!m || !fields) return ES_ERR_ARG;
+    const cudaMemcpyKind k = is_device_ptr(fields) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int f = 0; f < NFIELD; ++f) CK(cudaMemcpyAsync(m->f[f], fields + (size_t)f * m->ncell, m->ncell * 4, k, m->stream));
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f) {
+            if (!m->slab[a][f]) continue;
+            const int first = has_split(f, 0) ? 0 : 1;  // the split carrying the whole value
+            CK(launch_fill_slab(m->f[f], m->slab[a][f], a, m->nx, m->ny, m->nz, m->L, a == first, m->stream));
+        }
+    CK(cudaStreamSynchronize(m->stream));
+    return ES_OK;
+}
+
+int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces)
+{
+    int rc = run_checked_args(m, nt, dt, n_rcv);
+    if (rc != ES_OK) return rc;
+    cudaGetLastError();  // launch checks below must not see an earlier, unrelated error
+    if (n_rcv > 0 && (!rcv || !traces)) return ES_ERR_ARG;
+    if (!(dt > 0)) es_model_default_dt(m, &dt);
+    // stability of the staggered pseudo-spectral leapfrog: c dt |kappa_max| <= 2
+    const double s = std::sqrt(1.0 / (m->d[0] * m->d[0]) + 1.0 / (m->d[1] * m->d[1]) + 1.0 / (m->d[2] * m->d[2]));
+    if ((double)m->cp_max * dt * s > 2.0 / 3.14159265358979323846) return ES_ERR_UNSTABLE;
+    if (nt == 0) return ES_OK;
+
+    std::vector<int> h_rcv;
+    if ((rc = fetch(rcv, (size_t)n_rcv * 3, h_rcv, m->stream)) != ES_OK) return rc;
+    std::vector<long long> cells(n_rcv);
+    for (int r = 0; r < n_rcv; ++r) {
+        const int ix = h_rcv[3 * r], iy = h_rcv[3 * r + 1], iz = h_rcv[3 * r + 2];
+        if (ix < 0 || ix >= m->nx || iy < 0 || iy >= m->ny || iz < 0 || iz >= m->nz) return ES_ERR_ARG;
+        cells[r] = (long long)ix + (long long)m->nx * ((long long)iy + (long long)m->ny * iz);
+    }
+    if (n_rcv > m->rcv_cap) {
+        cudaFree(m->d_rcv);
+        m->d_rcv = nullptr;
+        m->rcv_cap = 0;
+        CK(cudaMalloc(&m->d_rcv, sizeof(long long) * n_rcv));
+        m->rcv_cap = n_rcv;
+    }
+    const size_t rec_n = (size_t)nt * 4 * n_rcv;
+    if (rec_n > m->rec_cap) {
+        cudaFree(m->d_rec);
+        m->d_rec = nullptr;
+        m->rec_cap = 0;
+        CK(cudaMalloc(&m->d_rec, rec_n * 4));
+        m->rec_cap = rec_n;
+    }
+    if (n_rcv > 0) CK(cudaMemcpyAsync(m->d_rcv, cells.data(), sizeof(long long) * n_rcv, cudaMemcpyHostToDevice, m->stream));
+
+    // PML factors for this dt (Sec. II-B; profile alpha0 (cref/d) xi^4)
+    const double cref = m->cref > 0 ? m->cref : (double)m->cp_max;
+    for (int a = 0; a < 3; ++a) {
+        const int n = axis_len(m, a), L = m->L;
+        std::vector<float> pc(n), ps(n);
+        for (int i = 0; i < n; ++i)
+            for (int st = 0; st < 2; ++st) {
+                const double x = i + (st ? 0.5 : 0.0);
+                double xi = 0.0;
+                if (L > 0) {
+                    if (x < L) xi = (L - x) / L;
+                    else if (x > n - 1 - L) xi = (x - (n - 1 - L)) / L;
+                    xi = std::min(xi, 1.0);
+                }
+                const double alpha = m->alpha0 * (cref / m->d[a]) * xi * xi * xi * xi;
+                (st ? ps : pc)[i] = (float)std::exp(-alpha * dt * 0.5);
+            }
+        CK(cudaMemcpyAsync(m->pc[a], pc.data(), n * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->ps[a], ps.data(), n * 4, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    if ((rc = upload_sources(m, dt)) != ES_OK) return rc;
+
+    // graphs: K steps, 1 step, 1 step with per-kernel events (the last step)
+    const long long start = m->steps_done;
+    const int K = 16;
+    cudaGraphExec_t gK = nullptr, g1 = nullptr, gT = nullptr;
+    const int body = nt - 1;
+    rc = ES_OK;
+    if (body >= K) rc = capture(m, K, (float)dt, n_rcv, start, false, &gK);
+    if (rc == ES_OK && body % K) rc = capture(m, 1, (float)dt, n_rcv, start, false, &g1);
+    if (rc == ES_OK) rc = capture(m, 1, (float)dt, n_rcv, start, true, &gT);
+    cudaError_t e = cudaSuccess;
+    if (rc == ES_OK) {
+        for (int i = 0; i < body / K && e == cudaSuccess; ++i) e = cudaGraphLaunch(gK, m->stream);
+        for (int i = 0; i < body % K && e == cudaSuccess; ++i) e = cudaGraphLaunch(g1, m->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gT, m->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->d_int + 2, 0, 4, m->stream);
+        if (e == cudaSuccess) e = launch_nonfinite(m->d_fields, m->ncell, m->d_int + 2, m->stream);
+    }
+    if (gK) cudaGraphExecDestroy(gK);
+    if (g1) cudaGraphExecDestroy(g1);
+    if (gT) cudaGraphExecDestroy(gT);
+    if (rc != ES_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "es_run launch");
+    m->steps_done += nt;
+
+    if (n_rcv > 0) {
+        const bool dev_out = is_device_ptr(traces);
+        float* dst = traces;
+        if (!dev_out) {
+            if (rec_n > m->out_cap) {
+                cudaFree(m->d_out);
+                m->d_out = nullptr;
+                m->out_cap = 0;
+                CK(cudaMalloc(&m->d_out, rec_n * 4));
+                m->out_cap = rec_n;
+            }
+            dst = m->d_out;
+        }
+        CK(launch_transpose_traces(m->d_rec, nt, n_rcv, dst, m->stream));
+        if (!dev_out) CK(cudaMemcpyAsync(traces, dst, rec_n * 4, cudaMemcpyDeviceToHost, m->stream));
+    }
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, m->d_int + 2, 4, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    for (int k = 0; k < m->n_last; ++k) CK(cudaEventElapsedTime(&m->last_ms[k], m->ev[2 * k], m->ev[2 * k + 1]));
+    return flag ? ES_ERR_UNSTABLE : ES_OK;
+}
+
+int es_last_step_kernel_ms(es_model* m, float* ms, int n)
+{
+    if (!m || !ms || n < 0) return ES_ERR_ARG;
+    const int k = std::min(n, m->n_last);
+    for (int i = 0; i < k; ++i) ms[i] = m->last_ms[i];
+    return k;
+}
+
+int es_kernels_per_step(const es_model* m)
+{
+    if (!m) return ES_ERR_ARG;
+    const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
+    return 8 + (has_force ? 1 : 0);
+}
+
+int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv)
+{
+    if (!m || !rcv || rx < 1 || ry < 1) return ES_ERR_ARG;
+    const int nx = m->nx, ny = m->ny, nz = m->nz, L = m->L;
+    std::vector<int> out((size_t)rx * ry * 3);
+    for (int jy = 0; jy < ry; ++jy)
+        for (int jx = 0; jx < rx; ++jx) {
+            const int ix = L + ((2 * jx + 1) * (nx - 2 * L)) / (2 * rx);
+            const int iy = L + ((2 * jy + 1) * (ny - 2 * L)) / (2 * ry);
+            auto at = [&](int z) { return m->cs[(size_t)ix + (size_t)nx * ((size_t)iy + (size_t)ny * z)]; };
+            if (at(0) != 0.f) return ES_ERR_ARG;
+            int iz = 0;
+            while (iz + 1 < nz && at(iz + 1) == 0.f) ++iz;
+            const size_t r = (size_t)jx + (size_t)rx * jy;
+            out[3 * r] = ix;
+            out[3 * r + 1] = iy;
+            out[3 * r + 2] = iz;
+        }
+    std::memcpy(rcv, out.data(), out.size() * sizeof(int));
+    return ES_OK;
+}
+
+int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* src_of_event, const float* amps,
+                 const float* t0s, int n_events, double dt, int n_out, float* gather, void* stream)
+{
+    if (!traces || !gather || n_src < 1 || n_rcv < 1 || nt < 1 || n_events < 0 || n_out < 1 || !(dt > 0))
+        return ES_ERR_ARG;
+    if (n_events > 0 && (!src_of_event || !amps || !t0s)) return ES_ERR_ARG;
+    cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> ev_src;
+    std::vector<float> ev_amp, ev_t0;
+    int rc;
+    if ((rc = fetch(src_of_event, (size_t)n_events, ev_src, st)) != ES_OK) return rc;
+    if ((rc = fetch(amps, (size_t)n_events, ev_amp, st)) != ES_OK) return rc;
+    if ((rc = fetch(t0s, (size_t)n_events, ev_t0, st)) != ES_OK) return rc;
+    std::vector<int> shift(n_events);
+    for (int e = 0; e < n_events; ++e) {
+        if (ev_src[e] < 0 || ev_src[e] >= n_src || !std::isfinite(ev_t0[e]) || !std::isfinite(ev_amp[e])) return ES_ERR_ARG;
+        const double k = std::floor((double)ev_t0[e] / dt + 0.5);  // k_e in FP64
+        shift[e] = (int)std::max(-2e9, std::min(2e9, k));
+    }
+    const size_t tr_n = (size_t)n_src * 4 * n_rcv * nt, g_n = (size_t)4 * n_rcv * n_out;
+    const bool dev_in = is_device_ptr(traces), dev_out = is_device_ptr(gather);
+    // one scratch block: events, and staging for host input / output
+    const size_t ev_bytes = (size_t)std::max(n_events, 1) * 12;
+    const size_t bytes = ev_bytes + (dev_in ? 0 : tr_n * 4 + 256) + (dev_out ? 0 : g_n * 4 + 256);
+    char* scratch = nullptr;
+    CK(cudaMalloc(&scratch, bytes));
+    int* d_src = (int*)scratch;
+    int* d_k = d_src + std::max(n_events, 1);
+    float* d_a = (float*)(d_k + std::max(n_events, 1));
+    char* p = scratch + (ev_bytes + 255) / 256 * 256;
+    const float* d_tr = traces;
+    if (!dev_in) { d_tr = (const float*)p; p += (tr_n * 4 + 255) / 256 * 256; }
+    float* d_g = dev_out ? gather : (float*)p;
+    cudaError_t e = cudaSuccess;
+    if (n_events > 0) {
+        e = cudaMemcpyAsync(d_src, ev_src.data(), n_events * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_k, shift.data(), n_events * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_a, ev_amp.data(), n_events * 4, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && !dev_in) e = cudaMemcpyAsync((void*)d_tr, traces, tr_n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_superpose(d_tr, n_src, n_rcv, nt, d_src, d_a, d_k, n_events, n_out, d_g, st);
+    if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(gather, d_g, g_n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "es_superpose");
+    return ES_OK;
+}
+
+int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out, void* stream)
+{
+    if (!f || !out || f == out || axis < 0 || axis > 2 || !(d > 0) || (shift != 1 && shift != -1)) return ES_ERR_ARG;
+    if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return ES_ERR_SIZE;
+    if (!is_device_ptr(f) || !is_device_ptr(out)) return ES_ERR_ARG;
+    cudaGetLastError();
+    int rc = ensure_prepared();
+    if (rc != ES_OK) return rc;
+    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    std::vector<float2> tw, hp, hm;
+    axis_tables(n, d, tw, hp, hm);
+    float2* tab = nullptr;
+    CK(cudaMalloc(&tab, 3 * n * 8));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpy(tab, tw.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tab + n, hp.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tab + 2 * n, hm.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        PassParams p;
+        std::memset(&p, 0, sizeof p);
+        p.nx = nx;
+        p.ny = ny;
+        p.nz = nz;
+        p.axis = axis;
+        p.n = n;
+        p.njobs = 1;
+        p.tw = tab;
+        p.hp = tab + n;
+        p.hm = tab + 2 * n;
+        p.job[0].src = f;
+        p.job[0].tgt[0] = out;
+        p.job[0].kind = JOB_STORE;
+        p.job[0].sign = shift;
+        e = launch_pass(p, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(tab);
+    if (e != cudaSuccess) return cuda_fail(e, "es_derivative");
+    return ES_OK;
+}
+
+}  // extern "C"

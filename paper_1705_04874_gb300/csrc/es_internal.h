@@ -1,0 +1,77 @@
+// Internal declarations shared by the kernel and host translation units of
+// libes.so.  Nothing here is part of the public C ABI (include/es.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace es {
+
+// Field numbering: velocity components, normal stresses, shear stresses.
+enum { VX, VY, VZ, SXX, SYY, SZZ, SXY, SXZ, SYZ, NFIELD };
+// Material arrays kept on the device.
+enum { M_BX, M_BY, M_BZ, M_LAM, M_MU, M_MUXY, M_MUXZ, M_MUYZ, NMAT };
+
+// What one derivative job does with D = D_axis^(sign) src in its epilogue.
+enum JobKind {
+    JOB_STORE = 0,   // tgt[0] = D (diagnostic)
+    JOB_SINGLE = 1,  // tgt[0] += dt coef[0] D (split-field PML in slabs)
+    JOB_NORMAL = 2   // sxx, syy, szz += dt (lambda + 2 mu [t == diag]) D
+};
+
+struct PassJob {
+    const float* src;     // field differentiated (total)
+    float* tgt[3];        // target totals
+    float* slab[3];       // target split parts along this axis, slab storage
+    const float* coef[2]; // JOB_SINGLE: coef[0]; JOB_NORMAL: lambda, mu
+    int kind;
+    int sign;             // +1: D(+) (result at +d/2), -1: D(-)
+    int stag;             // targets sit at half indices along this axis
+    int diag;             // JOB_NORMAL: target index receiving lambda + 2 mu
+};
+
+struct PassParams {
+    int nx, ny, nz;
+    int axis;             // 0 = x, 1 = y, 2 = z
+    int n;                // length along the axis
+    int njobs;
+    PassJob job[3];
+    const float2* tw;     // tw[m] = exp(-2 pi i m / n)
+    const float2* hp;     // i kappa exp(+i kappa d/2) / n
+    const float2* hm;     // i kappa exp(-i kappa d/2) / n
+    const float* pc;      // PML factors at whole indices along the axis
+    const float* ps;      // PML factors at half indices along the axis
+    int L;                // PML cells per face (slab width 2L+1, none if 0)
+    float dt;
+};
+
+// Plan of the two-stage FFT for an axis length (0 if unsupported).
+int plan_radices(int n, int* ra, int* rb);
+// Launches one pass (all jobs) along p.axis.  Returns a cudaError_t.
+cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
+// Opts every pass kernel into the shared memory it needs (once per device).
+cudaError_t prepare_pass_kernels();
+
+// ---- auxiliary kernels (aux_kernels.cu) ----
+struct SourceDev {
+    int kind;            // 0 moment, 1 force
+    long long cell;      // linear index
+    float m[6];          // moment (Mxx Myy Mzz Mxy Mxz Myz) or force scale per component
+    const float* w;      // wavelet samples (device)
+    int nw;
+};
+
+cudaError_t launch_inject(float* const* fields, const SourceDev* src, int nsrc, int kind,
+                          int* counter, int* cur, int advance, cudaStream_t st);
+cudaError_t launch_record(float* const* fields, const long long* rcv_cell, int n_rcv,
+                          const int* cur, long long start, float* rec, cudaStream_t st);
+cudaError_t launch_transpose_traces(const float* rec, int nt, int n_rcv, float* out,
+                                    cudaStream_t st);
+cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* ev_src,
+                             const float* ev_amp, const int* ev_shift, int n_events, int n_out,
+                             float* gather, cudaStream_t st);
+cudaError_t launch_nonfinite(float* const* fields, size_t n, int* flag, cudaStream_t st);
+cudaError_t launch_fill_slab(const float* total, float* slab, int axis, int nx, int ny, int nz,
+                             int L, int copy, cudaStream_t st);
+
+}  // namespace es

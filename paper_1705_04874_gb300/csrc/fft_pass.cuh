@@ -1,0 +1,518 @@
+// Fused pseudo-spectral derivative passes (Sec. II-A of Das, Chen & Hobson,
+// arXiv 1705.04874: Fourier-domain spatial derivatives on a staggered grid).
+//
+// One CTA owns a tile of 32 real pencils along the pass axis, packed two at a
+// time into 16 complex lines (line c = pencil 2c + i * pencil 2c+1).  For
+// each job it runs: forward FFT along the axis -> multiply by
+// i kappa exp(+/- i kappa d / 2) / n -> inverse FFT -> field-update epilogue.
+// Because the multiplier is Hermitian (a real field has a real derivative,
+// including at the Nyquist bin, where it is the real number -/+ pi / d), the
+// real and imaginary parts of the result are the derivatives of the two
+// packed pencils.
+//
+// The transform of length n = RA * RB is a two-stage Stockham autosort FFT
+// (radix RA with stride n/RA, then radix RB with twiddles exp(-2 pi i k r / n)).
+// Its last forward stage leaves each thread holding exactly the elements
+// b + q n/RB that the first stage of the inverse (run as a forward transform
+// of the conjugate, with the radices in reverse order) needs, so the
+// multiply and that stage happen in registers; shared memory is touched only
+// between stages.  The inverse's last stage ends on the same elements the
+// first forward stage loaded, so the epilogue writes where the loads read.
+//
+// Strided passes (y, z): a tile is 32 consecutive x (128-byte rows) by the
+// whole pencil; every global access of a warp is a full row segment.  The x
+// pass stages 32 whole x-lines (contiguous in memory) through shared memory
+// with float4 accesses and runs the same FFT core on the staged tile.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <type_traits>
+#include <utility>
+
+#include "es_internal.h"
+
+namespace es {
+
+// ---------------------------------------------------------------------------
+// compile-time twiddles W_R^M = exp(-2 pi i M / R)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double ce_cos_frac(long m, long r)
+{
+    // cos(2 pi m / r): exact at multiples of pi / 2, Taylor series otherwise
+    long mm = ((m % r) + r) % r;
+    if ((4 * mm) % r == 0) {
+        long q = (4 * mm) / r;
+        return q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+    }
+    double x = 6.283185307179586476925286766559 * (double)mm / (double)r;
+    if (2 * mm > r) x -= 6.283185307179586476925286766559;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 40; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ce_sin_frac(long m, long r)
+{
+    return ce_cos_frac(4 * m - r, 4 * r);  // sin(t) = cos(t - pi/2)
+}
+
+template <int R, int M>
+__device__ __forceinline__ float2 twc(float2 v)
+{
+    constexpr int mm = ((M % R) + R) % R;
+    if constexpr (mm == 0) {
+        return v;
+    } else if constexpr ((4 * mm) % R == 0) {
+        constexpr int q = (4 * mm) / R;  // rotation by -i q
+        if constexpr (q == 1) return make_float2(v.y, -v.x);
+        else if constexpr (q == 2) return make_float2(-v.x, -v.y);
+        else return make_float2(-v.y, v.x);
+    } else {
+        constexpr float c = (float)ce_cos_frac(mm, R);
+        constexpr float s = (float)(-ce_sin_frac(mm, R));
+        return make_float2(c * v.x - s * v.y, c * v.y + s * v.x);
+    }
+}
+
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f)
+{
+    sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+
+// ---------------------------------------------------------------------------
+// forward DFTs of small sizes in registers: a[k] <- sum_j a[j] W_R^(jk)
+// ---------------------------------------------------------------------------
+template <int R> struct Dft;
+
+template <> struct Dft<2> {
+    static __device__ __forceinline__ void run(float2* a)
+    {
+        float2 t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    }
+};
+
+template <> struct Dft<3> {
+    static __device__ __forceinline__ void run(float2* a)
+    {
+        constexpr float h = 0.86602540378443864676f;  // sqrt(3) / 2
+        float2 t1 = cadd(a[1], a[2]), t2 = csub(a[1], a[2]);
+        float2 m = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
+        float2 s = mul_mi(make_float2(h * t2.x, h * t2.y));
+        a[0] = cadd(a[0], t1);
+        a[1] = cadd(m, s);
+        a[2] = csub(m, s);
+    }
+};
+
+template <> struct Dft<4> {
+    static __device__ __forceinline__ void run(float2* a)
+    {
+        float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+        float2 s13 = cadd(a[1], a[3]), d13 = mul_mi(csub(a[1], a[3]));
+        a[0] = cadd(s02, s13);
+        a[2] = csub(s02, s13);
+        a[1] = cadd(d02, d13);
+        a[3] = csub(d02, d13);
+    }
+};
+
+template <> struct Dft<5> {
+    static __device__ __forceinline__ void run(float2* a)
+    {
+        constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+        constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+        constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+        constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+        float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+        float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+        float2 b1 = make_float2(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
+        float2 b2 = make_float2(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
+        float2 e1 = mul_mi(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+        float2 e2 = mul_mi(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+        a[0] = cadd(a[0], cadd(t1, t2));
+        a[1] = cadd(b1, e1);
+        a[4] = csub(b1, e1);
+        a[2] = cadd(b2, e2);
+        a[3] = csub(b2, e2);
+    }
+};
+
+// Composite R = P * Q in registers (Cooley-Tukey):
+// X[k1 + P k2] = sum_n2 W_Q^(n2 k2) W_R^(n2 k1) sum_n1 a[Q n1 + n2] W_P^(n1 k1)
+template <int P, int Q> struct DftPQ {
+    static __device__ __forceinline__ void run(float2* a)
+    {
+        constexpr int R = P * Q;
+        float2 B[Q][P];
+        sfor<Q>([&](auto n2) {
+            float2 v[P];
+            sfor<P>([&](auto n1) { v[n1] = a[Q * n1 + n2]; });
+            Dft<P>::run(v);
+            sfor<P>([&](auto k1) { B[n2][k1] = twc<R, decltype(n2)::value * decltype(k1)::value>(v[k1]); });
+        });
+        sfor<P>([&](auto k1) {
+            float2 v[Q];
+            sfor<Q>([&](auto n2) { v[n2] = B[n2][k1]; });
+            Dft<Q>::run(v);
+            sfor<Q>([&](auto k2) { a[k1 + P * k2] = v[k2]; });
+        });
+    }
+};
+template <> struct Dft<6> : DftPQ<2, 3> {};
+template <> struct Dft<8> : DftPQ<2, 4> {};
+template <> struct Dft<10> : DftPQ<2, 5> {};
+template <> struct Dft<12> : DftPQ<4, 3> {};
+template <> struct Dft<16> : DftPQ<4, 4> {};
+
+// ---------------------------------------------------------------------------
+// epilogues
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int slab_pos(int pos, int n, int L)
+{
+    // slab storage covers [0, L) and [n-1-L, n): every point whose whole- or
+    // half-index PML factor differs from 1
+    return pos < L ? pos : pos - (n - 1 - L) + L;
+}
+__device__ __forceinline__ bool in_slab(int pos, int n, int L)
+{
+    return L > 0 && (pos < L || pos >= n - 1 - L);
+}
+
+// index of (x, y, z) in the slab array of `axis` (slab coordinate sp)
+__device__ __forceinline__ size_t slab_index(int axis, int x, int y, int z, int sp, int nx, int ny, int S)
+{
+    if (axis == 0) return (size_t)sp + (size_t)S * ((size_t)y + (size_t)ny * z);
+    if (axis == 1) return (size_t)x + (size_t)nx * ((size_t)sp + (size_t)S * z);
+    return (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * sp);
+}
+
+// one cell: apply job J with derivative d at linear index q
+__device__ __forceinline__ void split_update(float* tot, float* slab, size_t si, float P, float inc)
+{
+    float s = slab[si];
+    float sn = P * (P * s + inc);
+    *tot += sn - s;
+    slab[si] = sn;
+}
+
+// Epilogue for a pair of x-adjacent cells (x even) at position `pos` along
+// the axis: q = linear index of the first cell, (x, y, z) its coordinates.
+__device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob& J, size_t q, int pos,
+                                              int x, int y, int z, float d0, float d1)
+{
+    if (J.kind == JOB_STORE) {
+        *reinterpret_cast<float2*>(J.tgt[0] + q) = make_float2(d0, d1);
+        return;
+    }
+    const float dt = p.dt;
+    const bool slab = in_slab(pos, p.n, p.L);
+    const int S = 2 * p.L + 1;
+    if (J.kind == JOB_SINGLE) {
+        float2 c = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
+        float2 t = *reinterpret_cast<float2*>(J.tgt[0] + q);
+        float i0 = dt * c.x * d0, i1 = dt * c.y * d1;
+        if (!slab) {
+            t.x += i0;
+            t.y += i1;
+        } else {
+            float P = __ldg((J.stag ? p.ps : p.pc) + pos);
+            size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            split_update(&t.x, J.slab[0], si, P, i0);
+            split_update(&t.y, J.slab[0], si + 1, P, i1);
+        }
+        *reinterpret_cast<float2*>(J.tgt[0] + q) = t;
+    } else {
+        float2 lam = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
+        float2 mu = __ldg(reinterpret_cast<const float2*>(J.coef[1] + q));
+        float P = slab ? __ldg(p.pc + pos) : 1.f;
+        size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            float2 c = lam;
+            if (t == J.diag) { c.x += 2.f * mu.x; c.y += 2.f * mu.y; }
+            float2 v = *reinterpret_cast<float2*>(J.tgt[t] + q);
+            float i0 = dt * c.x * d0, i1 = dt * c.y * d1;
+            if (!slab) {
+                v.x += i0;
+                v.y += i1;
+            } else {
+                split_update(&v.x, J.slab[t], si, P, i0);
+                split_update(&v.y, J.slab[t], si + 1, P, i1);
+            }
+            *reinterpret_cast<float2*>(J.tgt[t] + q) = v;
+        }
+    }
+}
+
+// Epilogue for one cell of the x pass.
+__device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos,
+                                             int y, int z, float d, float* tv, const float* cv0,
+                                             const float* cv1, int e)
+{
+    const float dt = p.dt;
+    const bool slab = in_slab(pos, p.n, p.L);
+    const int S = 2 * p.L + 1;
+    if (J.kind == JOB_SINGLE) {
+        float inc = dt * cv0[e] * d;
+        if (!slab) tv[e] += inc;
+        else {
+            float P = __ldg((J.stag ? p.ps : p.pc) + pos);
+            split_update(&tv[e], J.slab[0], slab_index(0, 0, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S), P, inc);
+        }
+    }
+    (void)q;
+}
+
+// ---------------------------------------------------------------------------
+// FFT core: stage helpers working on the [pos][line] shared layout
+// ---------------------------------------------------------------------------
+template <int RA, int RB, int CPAD>
+struct Core {
+    static constexpr int N = RA * RB;
+    static constexpr int BA = N / RA;   // stage-A butterflies = threads per line
+    static constexpr int BB = N / RB;   // stage-B butterflies
+    static constexpr int T = BA;
+    static constexpr int MB = (BB + T - 1) / T;
+
+    // stage A (radix RA, Stockham Ns = 1) on a[] (elements j + r BA), result
+    // to dst[(j RA + q)][c]
+    static __device__ __forceinline__ void stageA_store(float2* a, float2* dst, int j, int c)
+    {
+        Dft<RA>::run(a);
+#pragma unroll
+        for (int q = 0; q < RA; ++q) dst[(j * RA + q) * CPAD + c] = a[q];
+    }
+
+    // stage B (radix RB, Ns = RA) from src, spectral multiply, conjugate, first
+    // inverse stage (radix RB, Ns = 1), result to dst[(b RB + q)][c]
+    static __device__ __forceinline__ void stageB_mult_store(const float2* src, float2* dst, const float2* tw,
+                                                             const float2* H, int j, int c)
+    {
+#pragma unroll
+        for (int m = 0; m < MB; ++m) {
+            const int b = j + m * T;
+            if (BB % T == 0 || b < BB) {
+                float2 v[RB];
+                const int k = b % RA;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    float2 x = src[(b + r * BB) * CPAD + c];
+                    v[r] = r == 0 ? x : cmul(x, tw[k * r]);
+                }
+                Dft<RB>::run(v);
+#pragma unroll
+                for (int q = 0; q < RB; ++q) {
+                    float2 y = cmul(H[b + q * BB], v[q]);
+                    v[q] = make_float2(y.x, -y.y);
+                }
+                Dft<RB>::run(v);
+#pragma unroll
+                for (int q = 0; q < RB; ++q) dst[(b * RB + q) * CPAD + c] = v[q];
+            }
+        }
+    }
+
+    // last inverse stage (radix RA, Ns = RB): a[q] = conj(result) at element
+    // j + q BA, so a[q].x / a[q].y are the derivatives of pencils 2c / 2c+1
+    static __device__ __forceinline__ void stageA_inv(const float2* src, const float2* tw, float2* a, int j, int c)
+    {
+        const int k = j % RB;
+#pragma unroll
+        for (int r = 0; r < RA; ++r) {
+            float2 x = src[(j + r * BA) * CPAD + c];
+            a[r] = r == 0 ? x : cmul(x, tw[k * r]);
+        }
+        Dft<RA>::run(a);
+#pragma unroll
+        for (int q = 0; q < RA; ++q) a[q].y = -a[q].y;
+    }
+};
+
+constexpr int CP = 16;  // complex lines (pencil pairs) per CTA
+
+template <int RA, int RB>
+__host__ __device__ constexpr int pass_threads() { return (RA * RB / RA) * CP; }
+
+template <int RA, int RB, int CPAD>
+__host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * (2 * (size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
+
+// y and z passes
+template <int RA, int RB>
+__global__ void __launch_bounds__(pass_threads<RA, RB>())
+pass_strided(const __grid_constant__ PassParams p)
+{
+    using C = Core<RA, RB, CP>;
+    constexpr int N = C::N, BA = C::BA, T = C::T;
+    extern __shared__ float2 smem[];
+    float2* buf0 = smem;
+    float2* buf1 = buf0 + N * CP;
+    float2* s_tw = buf1 + N * CP;
+    float2* s_hp = s_tw + N;
+    float2* s_hm = s_hp + N;
+    const int tid = threadIdx.x;
+    const int c = tid % CP, j = tid / CP;
+    for (int i = tid; i < N; i += T * CP) {
+        s_tw[i] = p.tw[i];
+        s_hp[i] = p.hp[i];
+        s_hm[i] = p.hm[i];
+    }
+    const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
+    const int tx = blockIdx.x % ntx, outer = blockIdx.x / ntx;
+    const int x = tx * 2 * CP + 2 * c;
+    const bool valid = x < p.nx;
+    size_t base, est;
+    int y = 0, z = 0;
+    if (p.axis == 1) {
+        z = outer;
+        base = (size_t)x + (size_t)p.nx * p.ny * z;
+        est = (size_t)p.nx;
+    } else {
+        y = outer;
+        base = (size_t)x + (size_t)p.nx * y;
+        est = (size_t)p.nx * p.ny;
+    }
+    __syncthreads();
+    for (int jb = 0; jb < p.njobs; ++jb) {
+        const PassJob& J = p.job[jb];
+        float2 a[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r)
+            a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + base + (size_t)(j + r * BA) * est))
+                         : make_float2(0.f, 0.f);
+        C::stageA_store(a, buf0, j, c);
+        __syncthreads();
+        C::stageB_mult_store(buf0, buf1, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
+        __syncthreads();
+        C::stageA_inv(buf1, s_tw, a, j, c);
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < RA; ++q) {
+                const int pos = j + q * BA;
+                if (p.axis == 1) y = pos; else z = pos;
+                epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y);
+            }
+        }
+    }
+}
+
+// x pass: 32 consecutive x-lines (line = y + ny z) staged through shared memory
+template <int RA, int RB>
+__global__ void __launch_bounds__(pass_threads<RA, RB>())
+pass_x(const __grid_constant__ PassParams p)
+{
+    constexpr int CPAD = CP + 1;
+    using C = Core<RA, RB, CPAD>;
+    constexpr int N = C::N, T = C::T, NT = T * CP;
+    constexpr int LINES = 2 * CP;
+    constexpr int ITEMS = LINES * N / 4;  // float4 chunks in the tile
+    extern __shared__ float2 smem[];
+    float2* buf0 = smem;
+    float2* buf1 = buf0 + N * CPAD;
+    float2* s_tw = buf1 + N * CPAD;
+    float2* s_hp = s_tw + N;
+    float2* s_hm = s_hp + N;
+    const int tid = threadIdx.x;
+    const int c = tid % CP, j = tid / CP;
+    for (int i = tid; i < N; i += NT) {
+        s_tw[i] = p.tw[i];
+        s_hp[i] = p.hp[i];
+        s_hm[i] = p.hm[i];
+    }
+    const int nlines = p.ny * p.nz;
+    const int line0 = blockIdx.x * LINES;
+    for (int jb = 0; jb < p.njobs; ++jb) {
+        const PassJob& J = p.job[jb];
+        // stage the tile: chunk it -> (line r, x = 4 * chunk)
+        float* b0 = reinterpret_cast<float*>(buf0);
+        for (int it = tid; it < ITEMS; it += NT) {
+            const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+            const int xx = (hi * 4 + lo) * 4;
+            const int line = line0 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + (size_t)line * N + xx));
+            b0[((xx + 0) * CPAD) * 2 + r] = v.x;
+            b0[((xx + 1) * CPAD) * 2 + r] = v.y;
+            b0[((xx + 2) * CPAD) * 2 + r] = v.z;
+            b0[((xx + 3) * CPAD) * 2 + r] = v.w;
+        }
+        __syncthreads();
+        float2 a[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) a[r] = buf0[(j + r * C::BA) * CPAD + c];
+        C::stageA_store(a, buf1, j, c);
+        __syncthreads();
+        C::stageB_mult_store(buf1, buf0, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
+        __syncthreads();
+        C::stageA_inv(buf0, s_tw, a, j, c);
+#pragma unroll
+        for (int q = 0; q < RA; ++q) buf1[(j + q * C::BA) * CPAD + c] = a[q];
+        __syncthreads();
+        const float* b1 = reinterpret_cast<const float*>(buf1);
+        for (int it = tid; it < ITEMS; it += NT) {
+            const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+            const int xx = (hi * 4 + lo) * 4;
+            const int line = line0 + r;
+            if (line >= nlines) continue;
+            float d[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) d[e] = b1[((xx + e) * CPAD) * 2 + r];
+            const size_t q0 = (size_t)line * N + xx;
+            const int y = line % p.ny, z = line / p.ny;
+            if (J.kind == JOB_STORE) {
+                *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(d[0], d[1], d[2], d[3]);
+            } else if (J.kind == JOB_SINGLE) {
+                float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+                float4 t4 = *reinterpret_cast<float4*>(J.tgt[0] + q0);
+                float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) epilogue_one(p, J, q0 + e, xx + e, y, z, d[e], tv, cv, nullptr, e);
+                *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            } else {
+                float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+                float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
+                float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+                float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+                const int S = 2 * p.L + 1;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    float4 t4 = *reinterpret_cast<float4*>(J.tgt[t] + q0);
+                    float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int pos = xx + e;
+                        const float cc = lv[e] + (t == J.diag ? 2.f * mv[e] : 0.f);
+                        const float inc = p.dt * cc * d[e];
+                        if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
+                        else split_update(&tv[e], J.slab[t],
+                                          slab_index(0, 0, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S),
+                                          __ldg(p.pc + pos), inc);
+                    }
+                    *reinterpret_cast<float4*>(J.tgt[t] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+                }
+            }
+        }
+        // the next job's staging writes buf0, last read before the barrier above;
+        // its stage A writes buf1 only after its own staging barrier
+    }
+}
+
+}  // namespace es

@@ -1,0 +1,59 @@
+"""The C ABI builds, loads without a GPU, and exports every entry point that
+include/es.h declares; host-side argument checks answer without touching a
+device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_04874_gb300 import es
+    return es._load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "es.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(es_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("es_model_create", "es_source_set", "es_run", "es_superpose", "es_model_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1705_04874_gb300 import es
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(declared_symbols()) == set(es.exported_symbols())
+
+
+def test_status_strings(lib):
+    for s in range(0, -8, -1):
+        assert lib.es_status_string(s).decode() not in ("", "unknown status")
+    assert lib.es_status_string(5).decode() == "unknown status"
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1705_04874_gb300 import es
+    h = ctypes.c_void_p()
+    # null inputs / bad sizes are rejected before any device work
+    assert lib.es_model_create(None, None, None, 32, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
+    a = np.ones(8, np.float32)
+    p = ctypes.c_void_p(a.ctypes.data)
+    assert lib.es_model_create(p, p, p, 33, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_SIZE
+    assert lib.es_model_create(p, p, p, 32, 32, 32, -1.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
+    assert lib.es_model_create(p, p, p, 32, 32, 32, 10.0, 15, ctypes.byref(h)) == es.ES_ERR_ARG
+    assert lib.es_superpose(None, 1, 1, 1, None, None, None, 0, 0.1, 1, None, None) == es.ES_ERR_ARG
+    assert lib.es_derivative(p, 32, 32, 32, 3, 1.0, 1, p, None) == es.ES_ERR_ARG
+    assert lib.es_derivative(p, 30, 32, 32, 0, 1.0, 1, ctypes.c_void_p(a.ctypes.data + 4), None) == es.ES_ERR_SIZE
+    assert lib.es_run(None, 10, 0.0, None, 0, None) == es.ES_ERR_ARG
+    assert lib.es_kernels_per_step(None) == es.ES_ERR_ARG

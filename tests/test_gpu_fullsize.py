@@ -1,0 +1,123 @@
+"""Parity at the benchmark's full grid sizes, in the launch configuration the
+benchmark times (es_run through the C ABI): 128^3 and 256^3 marine models.
+The oracle cannot run thousands of steps at these sizes in a test, so the
+whole field state is compared after a few steps, and properties that hold at
+any length (exact linearity and delay, receiver maps, energy conservation with
+the PML off) are checked over longer runs on the GPU alone."""
+import numpy as np
+import pytest
+
+from paper_1705_04874_gb300 import synth
+from conftest import cfl_dt, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def es():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_04874_gb300 import es as _es
+    _es._load()
+    return _es
+
+
+def _field_parity(es, orc, n, pml, mt, nt, seed, rx):
+    rho, cp, cs = synth.marine_model(n, seed=seed)
+    dt = cfl_dt(cp, 10.0)
+    box = synth.reservoir_box((n, n, n), pml)
+    pos = tuple((lo + hi) // 2 for lo, hi in box)
+    w = synth.ricker(nt, dt, 30.0, t0=4 * dt)
+    with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
+        rcv = m.seabed_receivers(rx, rx)
+        m.source_set(pos, mt, w)
+        traces = m.run(nt, dt, rcv)
+        st = m.state_get()
+    assert np.array_equal(rcv, orc.seabed_receivers(cs, pml, rx, rx))
+    ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml,
+                       sources=[dict(kind="moment", pos=pos, m=mt, w=w)], receivers=rcv,
+                       state=np.zeros((9, n, n, n)))
+    for f in range(9):
+        assert rel_l2(st[f], ref["state"][f]) < 1e-4, f
+    assert np.isfinite(traces).all()
+
+
+def test_marine_128_field_parity(es, orc):
+    """128^3 marine model, PML 10, double couple (strike 30, dip 60, rake 90)
+    at the reservoir-box centre, 32 x 32 seabed receivers."""
+    _field_parity(es, orc, 128, 10, synth.double_couple_sdr(30, 60, 90), 60, 1, 32)
+
+
+def test_marine_256_field_parity(es, orc):
+    """256^3 marine model, PML 12, random strike/dip/rake double couple,
+    64 x 64 seabed receivers: the benchmark's grid and launch configuration."""
+    mt = synth.random_dc(synth.SplitMix64(2))
+    _field_parity(es, orc, 256, 12, mt, 10, 1, 64)
+
+
+def test_marine_256_linearity_over_many_steps(es):
+    n, pml, nt = 256, 12, 400
+    rho, cp, cs = synth.marine_model(n, seed=1)
+    dt = cfl_dt(cp, 10.0)
+    mt = synth.random_dc(synth.SplitMix64(2))
+    box = synth.reservoir_box((n, n, n), pml)
+    pos = tuple((lo + hi) // 2 for lo, hi in box)
+    w = synth.ricker(nt, dt, 30.0)
+    k = 37
+    with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
+        rcv = m.seabed_receivers(64, 64)
+        m.source_set(pos, mt, w)
+        a = m.run(nt, dt, rcv)
+        m.state_reset()
+        m.source_set(pos, mt, (2 * w).astype(np.float32))
+        b = m.run(nt, dt, rcv)
+        m.state_reset()
+        m.source_set(pos, mt, np.concatenate([np.zeros(k, np.float32), w])[:nt])
+        c = m.run(nt, dt, rcv)
+    assert np.abs(a).max() > 0
+    assert np.array_equal(b, 2 * a)
+    assert np.array_equal(c[..., k:], a[..., :nt - k])
+
+
+def _energy(orc_mats, prev, cur):
+    """Discrete energy at step n from the states at n and n+1 (v^{n-1/2},
+    sigma^n and v^{n+1/2}), PML off."""
+    lam, mu = orc_mats["lam"], orc_mats["mu"]
+    e = 0.0
+    for c, b in enumerate(("bx", "by", "bz")):
+        e += 0.5 * np.sum(prev[c].astype(np.float64) * cur[c] / orc_mats[b])
+    s = prev[3:].astype(np.float64)
+    tr = s[0] + s[1] + s[2]
+    solid = mu > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        en = np.where(solid, (s[0] ** 2 + s[1] ** 2 + s[2] ** 2) / (2 * mu)
+                      - lam / (2 * mu * (3 * lam + 2 * mu)) * tr ** 2, (tr / 3) ** 2 / lam)
+    e += 0.5 * np.sum(en)
+    for c, name in enumerate(("muxy", "muxz", "muyz")):
+        me = orc_mats[name]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            e += 0.5 * np.sum(np.where(me > 0, s[3 + c] ** 2 / me, 0.0))
+    return e
+
+
+def test_energy_conserved_without_pml_128(es, orc):
+    n = 128
+    rho, cp, cs = synth.marine_model(n, seed=4)
+    dt = cfl_dt(cp, 10.0)
+    nw = 120
+    w = synth.ricker(nw, dt, 30.0)
+    mats = orc.materials(rho, cp, cs)
+    with es.Model(rho, cp, cs, dx=10.0, pml=0) as m:
+        m.source_set((64, 64, 60), synth.double_couple_sdr(45, 50, 10), w)
+        m.run(nw + 10, dt)
+        es_ = []
+        for _ in range(3):
+            s0 = m.state_get()
+            m.run(1, dt)
+            s1 = m.state_get()
+            es_.append(_energy(mats, s0, s1))
+            m.run(300, dt)
+    es_ = np.array(es_)
+    assert es_.min() > 0
+    assert (es_.max() - es_.min()) / es_.max() < 2e-4, es_
