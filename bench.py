@@ -290,9 +290,13 @@ def main():
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
+        # ncu DRAM bytes per launch, valid only for the kernel source they were taken on
+        import hashlib
         try:
-            t = json.load(open(prof)).get(f"{args.workload}:{dom}")
-            traffic = t
+            rec = json.load(open(prof))
+            src = open(os.path.join(ROOT, "paper_1705_04874_gb300", "csrc", "fft_pass.cuh"), "rb").read()
+            if hashlib.sha256(src).hexdigest().startswith(rec.get("kernel_source_sha256_prefix", "-")):
+                traffic = rec.get(f"{args.workload}:{dom}")
         except (OSError, ValueError):
             traffic = None
     kernels = {k: {"ms": round(float(kmean[i]), 5),

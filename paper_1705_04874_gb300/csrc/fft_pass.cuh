@@ -262,27 +262,57 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
     }
 }
 
-// Epilogue for one cell of the x pass.
-__device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos,
-                                             int y, int z, float d, float* tv, const float* cv0,
-                                             const float* cv1, int e)
+// Epilogue for 4 x-consecutive cells of one x line (x pass): q0 = linear
+// index of the first, pos0 its x, d[] the derivatives.
+__device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob& J, size_t q0, int pos0,
+                                              int y, int z, const float* d)
 {
+    if (J.kind == JOB_STORE) {
+        *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(d[0], d[1], d[2], d[3]);
+        return;
+    }
     const float dt = p.dt;
-    const bool slab = in_slab(pos, p.n, p.L);
     const int S = 2 * p.L + 1;
+    const size_t srow = (size_t)S * ((size_t)y + (size_t)p.ny * z);
     if (J.kind == JOB_SINGLE) {
-        float inc = dt * cv0[e] * d;
-        if (!slab) tv[e] += inc;
-        else {
-            float P = __ldg((J.stag ? p.ps : p.pc) + pos);
-            split_update(&tv[e], J.slab[0], slab_index(0, 0, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S), P, inc);
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+        const float4 t4 = *reinterpret_cast<const float4*>(J.tgt[0] + q0);
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+        float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int pos = pos0 + e;
+            const float inc = dt * cv[e] * d[e];
+            if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
+            else split_update(&tv[e], J.slab[0], srow + slab_pos(pos, p.n, p.L),
+                              __ldg((J.stag ? p.ps : p.pc) + pos), inc);
+        }
+        *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+    } else {
+        const float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+        const float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
+        const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+        const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const float4 t4 = *reinterpret_cast<const float4*>(J.tgt[t] + q0);
+            float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int pos = pos0 + e;
+                const float cc = lv[e] + (t == J.diag ? 2.f * mv[e] : 0.f);
+                const float inc = dt * cc * d[e];
+                if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
+                else split_update(&tv[e], J.slab[t], srow + slab_pos(pos, p.n, p.L), __ldg(p.pc + pos), inc);
+            }
+            *reinterpret_cast<float4*>(J.tgt[t] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
         }
     }
-    (void)q;
 }
 
 // ---------------------------------------------------------------------------
-// FFT core: stage helpers working on the [pos][line] shared layout
+// FFT core on the shared [pos][line] layout (one buffer, updated in place:
+// every stage reads all its inputs, the block synchronises, then it writes)
 // ---------------------------------------------------------------------------
 template <int RA, int RB, int CPAD>
 struct Core {
@@ -292,52 +322,59 @@ struct Core {
     static constexpr int T = BA;
     static constexpr int MB = (BB + T - 1) / T;
 
-    // stage A (radix RA, Stockham Ns = 1) on a[] (elements j + r BA), result
-    // to dst[(j RA + q)][c]
-    static __device__ __forceinline__ void stageA_store(float2* a, float2* dst, int j, int c)
+    // stage A (radix RA, Stockham Ns = 1): a[] holds elements j + r BA; the
+    // result goes to element j RA + q
+    static __device__ __forceinline__ void stageA_store(const float2* a, float2* buf, int j, int c)
     {
-        Dft<RA>::run(a);
 #pragma unroll
-        for (int q = 0; q < RA; ++q) dst[(j * RA + q) * CPAD + c] = a[q];
+        for (int q = 0; q < RA; ++q) buf[(j * RA + q) * CPAD + c] = a[q];
     }
 
-    // stage B (radix RB, Ns = RA) from src, spectral multiply, conjugate, first
-    // inverse stage (radix RB, Ns = 1), result to dst[(b RB + q)][c]
-    static __device__ __forceinline__ void stageB_mult_store(const float2* src, float2* dst, const float2* tw,
-                                                             const float2* H, int j, int c)
+    // stage B (radix RB, Ns = RA), spectral multiply, conjugate, first inverse
+    // stage (radix RB, Ns = 1), all in registers
+    static __device__ __forceinline__ void stageB_compute(const float2* buf, float2 (&v)[MB][RB], const float2* tw,
+                                                          const float2* H, int j, int c)
     {
 #pragma unroll
         for (int m = 0; m < MB; ++m) {
             const int b = j + m * T;
             if (BB % T == 0 || b < BB) {
-                float2 v[RB];
                 const int k = b % RA;
 #pragma unroll
                 for (int r = 0; r < RB; ++r) {
-                    float2 x = src[(b + r * BB) * CPAD + c];
-                    v[r] = r == 0 ? x : cmul(x, tw[k * r]);
+                    const float2 x = buf[(b + r * BB) * CPAD + c];
+                    v[m][r] = r == 0 ? x : cmul(x, tw[k * r]);
                 }
-                Dft<RB>::run(v);
+                Dft<RB>::run(v[m]);
 #pragma unroll
                 for (int q = 0; q < RB; ++q) {
-                    float2 y = cmul(H[b + q * BB], v[q]);
-                    v[q] = make_float2(y.x, -y.y);
+                    const float2 y = cmul(H[b + q * BB], v[m][q]);
+                    v[m][q] = make_float2(y.x, -y.y);
                 }
-                Dft<RB>::run(v);
+                Dft<RB>::run(v[m]);
+            }
+        }
+    }
+    static __device__ __forceinline__ void stageB_store(float2* buf, const float2 (&v)[MB][RB], int j, int c)
+    {
 #pragma unroll
-                for (int q = 0; q < RB; ++q) dst[(b * RB + q) * CPAD + c] = v[q];
+        for (int m = 0; m < MB; ++m) {
+            const int b = j + m * T;
+            if (BB % T == 0 || b < BB) {
+#pragma unroll
+                for (int q = 0; q < RB; ++q) buf[(b * RB + q) * CPAD + c] = v[m][q];
             }
         }
     }
 
     // last inverse stage (radix RA, Ns = RB): a[q] = conj(result) at element
     // j + q BA, so a[q].x / a[q].y are the derivatives of pencils 2c / 2c+1
-    static __device__ __forceinline__ void stageA_inv(const float2* src, const float2* tw, float2* a, int j, int c)
+    static __device__ __forceinline__ void stageA_inv(const float2* buf, const float2* tw, float2* a, int j, int c)
     {
         const int k = j % RB;
 #pragma unroll
         for (int r = 0; r < RA; ++r) {
-            float2 x = src[(j + r * BA) * CPAD + c];
+            const float2 x = buf[(j + r * BA) * CPAD + c];
             a[r] = r == 0 ? x : cmul(x, tw[k * r]);
         }
         Dft<RA>::run(a);
@@ -351,29 +388,43 @@ constexpr int CP = 16;  // complex lines (pencil pairs) per CTA
 template <int RA, int RB>
 __host__ __device__ constexpr int pass_threads() { return (RA * RB / RA) * CP; }
 
-template <int RA, int RB, int CPAD>
-__host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * (2 * (size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
-
-// y and z passes
+// blocks per SM the register budget is sized for (about 1024 threads per SM)
 template <int RA, int RB>
-__global__ void __launch_bounds__(pass_threads<RA, RB>())
+__host__ __device__ constexpr int pass_min_blocks()
+{
+    return pass_threads<RA, RB>() >= 1024 ? 1 : 1024 / pass_threads<RA, RB>();
+}
+
+template <int RA, int RB, int CPAD>
+__host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * ((size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
+
+template <int N>
+__device__ __forceinline__ void load_tables(const PassParams& p, float2* s_tw, float2* s_hp, float2* s_hm, int tid,
+                                            int nthreads)
+{
+    for (int i = tid; i < N; i += nthreads) {
+        s_tw[i] = p.tw[i];
+        s_hp[i] = p.hp[i];
+        s_hm[i] = p.hm[i];
+    }
+}
+
+// y and z passes: blockIdx.x = tile (32 consecutive x at one z (y pass) or
+// one y (z pass)), blockIdx.y = job
+template <int RA, int RB>
+__global__ void __launch_bounds__(pass_threads<RA, RB>(), pass_min_blocks<RA, RB>())
 pass_strided(const __grid_constant__ PassParams p)
 {
     using C = Core<RA, RB, CP>;
     constexpr int N = C::N, BA = C::BA, T = C::T;
     extern __shared__ float2 smem[];
-    float2* buf0 = smem;
-    float2* buf1 = buf0 + N * CP;
-    float2* s_tw = buf1 + N * CP;
+    float2* buf = smem;
+    float2* s_tw = buf + N * CP;
     float2* s_hp = s_tw + N;
     float2* s_hm = s_hp + N;
     const int tid = threadIdx.x;
     const int c = tid % CP, j = tid / CP;
-    for (int i = tid; i < N; i += T * CP) {
-        s_tw[i] = p.tw[i];
-        s_hp[i] = p.hp[i];
-        s_hm[i] = p.hm[i];
-    }
+    const PassJob& J = p.job[blockIdx.y];
     const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
     const int tx = blockIdx.x % ntx, outer = blockIdx.x / ntx;
     const int x = tx * 2 * CP + 2 * c;
@@ -389,129 +440,97 @@ pass_strided(const __grid_constant__ PassParams p)
         base = (size_t)x + (size_t)p.nx * y;
         est = (size_t)p.nx * p.ny;
     }
+    float2 a[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + base + (size_t)(j + r * BA) * est))
+                     : make_float2(0.f, 0.f);
+    load_tables<N>(p, s_tw, s_hp, s_hm, tid, T * CP);
+    Dft<RA>::run(a);
+    C::stageA_store(a, buf, j, c);
     __syncthreads();
-    for (int jb = 0; jb < p.njobs; ++jb) {
-        const PassJob& J = p.job[jb];
-        float2 a[RA];
-#pragma unroll
-        for (int r = 0; r < RA; ++r)
-            a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + base + (size_t)(j + r * BA) * est))
-                         : make_float2(0.f, 0.f);
-        C::stageA_store(a, buf0, j, c);
+    {
+        float2 v[C::MB][RB];
+        C::stageB_compute(buf, v, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
         __syncthreads();
-        C::stageB_mult_store(buf0, buf1, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
-        __syncthreads();
-        C::stageA_inv(buf1, s_tw, a, j, c);
-        if (valid) {
+        C::stageB_store(buf, v, j, c);
+    }
+    __syncthreads();
+    C::stageA_inv(buf, s_tw, a, j, c);
+    if (!valid) return;
 #pragma unroll
-            for (int q = 0; q < RA; ++q) {
-                const int pos = j + q * BA;
-                if (p.axis == 1) y = pos; else z = pos;
-                epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y);
-            }
-        }
+    for (int q = 0; q < RA; ++q) {
+        const int pos = j + q * BA;
+        if (p.axis == 1) y = pos; else z = pos;
+        epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y);
     }
 }
 
-// x pass: 32 consecutive x-lines (line = y + ny z) staged through shared memory
+// x pass: blockIdx.x = tile of 32 consecutive x-lines (line = y + ny z, so
+// the tile is one contiguous block of memory), blockIdx.y = job
 template <int RA, int RB>
-__global__ void __launch_bounds__(pass_threads<RA, RB>())
+__global__ void __launch_bounds__(pass_threads<RA, RB>(), pass_min_blocks<RA, RB>())
 pass_x(const __grid_constant__ PassParams p)
 {
-    constexpr int CPAD = CP + 1;
+    constexpr int CPAD = CP + 1;  // row padding: the staging transposes stay conflict-free
     using C = Core<RA, RB, CPAD>;
-    constexpr int N = C::N, T = C::T, NT = T * CP;
+    constexpr int N = C::N, BA = C::BA, NT = C::T * CP;
     constexpr int LINES = 2 * CP;
     constexpr int ITEMS = LINES * N / 4;  // float4 chunks in the tile
     extern __shared__ float2 smem[];
-    float2* buf0 = smem;
-    float2* buf1 = buf0 + N * CPAD;
-    float2* s_tw = buf1 + N * CPAD;
+    float2* buf = smem;
+    float2* s_tw = buf + N * CPAD;
     float2* s_hp = s_tw + N;
     float2* s_hm = s_hp + N;
     const int tid = threadIdx.x;
     const int c = tid % CP, j = tid / CP;
-    for (int i = tid; i < N; i += NT) {
-        s_tw[i] = p.tw[i];
-        s_hp[i] = p.hp[i];
-        s_hm[i] = p.hm[i];
-    }
+    const PassJob& J = p.job[blockIdx.y];
     const int nlines = p.ny * p.nz;
     const int line0 = blockIdx.x * LINES;
-    for (int jb = 0; jb < p.njobs; ++jb) {
-        const PassJob& J = p.job[jb];
-        // stage the tile: chunk it -> (line r, x = 4 * chunk)
-        float* b0 = reinterpret_cast<float*>(buf0);
-        for (int it = tid; it < ITEMS; it += NT) {
-            const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
-            const int xx = (hi * 4 + lo) * 4;
-            const int line = line0 + r;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + (size_t)line * N + xx));
-            b0[((xx + 0) * CPAD) * 2 + r] = v.x;
-            b0[((xx + 1) * CPAD) * 2 + r] = v.y;
-            b0[((xx + 2) * CPAD) * 2 + r] = v.z;
-            b0[((xx + 3) * CPAD) * 2 + r] = v.w;
-        }
+    // chunk it -> line r = (it / 4) % 32, x = 4 (4 (it / 128) + it % 4): a warp
+    // covers 8 lines x 64 contiguous bytes, and its shared stores hit 32 banks
+    float* bf = reinterpret_cast<float*>(buf);
+    for (int it = tid; it < ITEMS; it += NT) {
+        const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+        const int xx = (hi * 4 + lo) * 4;
+        const int line = line0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + (size_t)line * N + xx));
+        bf[((xx + 0) * CPAD) * 2 + r] = v.x;
+        bf[((xx + 1) * CPAD) * 2 + r] = v.y;
+        bf[((xx + 2) * CPAD) * 2 + r] = v.z;
+        bf[((xx + 3) * CPAD) * 2 + r] = v.w;
+    }
+    load_tables<N>(p, s_tw, s_hp, s_hm, tid, NT);
+    __syncthreads();
+    float2 a[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) a[r] = buf[(j + r * BA) * CPAD + c];
+    Dft<RA>::run(a);
+    __syncthreads();
+    C::stageA_store(a, buf, j, c);
+    __syncthreads();
+    {
+        float2 v[C::MB][RB];
+        C::stageB_compute(buf, v, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
         __syncthreads();
-        float2 a[RA];
+        C::stageB_store(buf, v, j, c);
+    }
+    __syncthreads();
+    C::stageA_inv(buf, s_tw, a, j, c);
+    __syncthreads();
 #pragma unroll
-        for (int r = 0; r < RA; ++r) a[r] = buf0[(j + r * C::BA) * CPAD + c];
-        C::stageA_store(a, buf1, j, c);
-        __syncthreads();
-        C::stageB_mult_store(buf1, buf0, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
-        __syncthreads();
-        C::stageA_inv(buf0, s_tw, a, j, c);
+    for (int q = 0; q < RA; ++q) buf[(j + q * BA) * CPAD + c] = a[q];
+    __syncthreads();
+    for (int it = tid; it < ITEMS; it += NT) {
+        const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+        const int xx = (hi * 4 + lo) * 4;
+        const int line = line0 + r;
+        if (line >= nlines) continue;
+        float d[4];
 #pragma unroll
-        for (int q = 0; q < RA; ++q) buf1[(j + q * C::BA) * CPAD + c] = a[q];
-        __syncthreads();
-        const float* b1 = reinterpret_cast<const float*>(buf1);
-        for (int it = tid; it < ITEMS; it += NT) {
-            const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
-            const int xx = (hi * 4 + lo) * 4;
-            const int line = line0 + r;
-            if (line >= nlines) continue;
-            float d[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) d[e] = b1[((xx + e) * CPAD) * 2 + r];
-            const size_t q0 = (size_t)line * N + xx;
-            const int y = line % p.ny, z = line / p.ny;
-            if (J.kind == JOB_STORE) {
-                *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(d[0], d[1], d[2], d[3]);
-            } else if (J.kind == JOB_SINGLE) {
-                float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
-                float4 t4 = *reinterpret_cast<float4*>(J.tgt[0] + q0);
-                float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                float tv[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) epilogue_one(p, J, q0 + e, xx + e, y, z, d[e], tv, cv, nullptr, e);
-                *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
-            } else {
-                float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
-                float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
-                float lv[4] = {l4.x, l4.y, l4.z, l4.w};
-                float mv[4] = {m4.x, m4.y, m4.z, m4.w};
-                const int S = 2 * p.L + 1;
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    float4 t4 = *reinterpret_cast<float4*>(J.tgt[t] + q0);
-                    float tv[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int pos = xx + e;
-                        const float cc = lv[e] + (t == J.diag ? 2.f * mv[e] : 0.f);
-                        const float inc = p.dt * cc * d[e];
-                        if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
-                        else split_update(&tv[e], J.slab[t],
-                                          slab_index(0, 0, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S),
-                                          __ldg(p.pc + pos), inc);
-                    }
-                    *reinterpret_cast<float4*>(J.tgt[t] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
-                }
-            }
-        }
-        // the next job's staging writes buf0, last read before the barrier above;
-        // its stage A writes buf1 only after its own staging barrier
+        for (int e = 0; e < 4; ++e) d[e] = bf[((xx + e) * CPAD) * 2 + r];
+        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d);
     }
 }
 
