@@ -125,6 +125,34 @@ int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* s
                  const float* amps, const float* t0s, int n_events, double dt, int n_out,
                  float* gather, void* stream);
 
+/* The same superposition as es_superpose, for callers that cannot allocate
+ * device memory: a caller whose device memory is owned by its own pool
+ * allocator (which may leave no headroom, and whose budget a library
+ * cudaMalloc would break), or a caller streaming work where the implicit
+ * device synchronisation of cudaMalloc / cudaFree would stall its other
+ * streams.  This entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The paper has no counterpart; it is a service of this
+ * library.
+ * - traces, src_of_event, amps, t0s and gather must all be device pointers
+ *   (ES_ERR_ARG otherwise); layouts and results are those of es_superpose,
+ *   and the output matches it exactly.
+ * - Scratch: a fixed device array of ES_NOALLOC_MAX_EVENTS + 64 ints
+ *   (~256 KB), allocated when the library is loaded and held by every GPU
+ *   that loads it until the process exits.  n_events > ES_NOALLOC_MAX_EVENTS
+ *   is ES_ERR_ARG.
+ * - The first call on a device looks up that array's device address; make
+ *   the first call on each device before any stream capture.
+ * - Every call shares the array (each call clears what it needs): calls that
+ *   overlap on the GPU (other streams, other host threads) race; order them.
+ * - The call waits for an argument check on the device before launching, so
+ *   it returns after queueing the superposition (stream-ordered output); on
+ *   ES_ERR_ARG (bad source index, non-finite amplitude or time) nothing is
+ *   written to gather. */
+#define ES_NOALLOC_MAX_EVENTS 65536
+int es_superpose_noalloc(const float* traces, int n_src, int n_rcv, int nt, const int* src_of_event,
+                         const float* amps, const float* t0s, int n_events, double dt, int n_out,
+                         float* gather, void* stream);
+
 /* Seabed receiver grid (Sec. II-B, Fig. 2): rx * ry receivers over the
  * non-PML interior, ix_i = pml + ((2i+1)(nx - 2 pml)) / (2 rx) (integer
  * division), likewise in y; iz = the last cell of the top run of cs == 0 in

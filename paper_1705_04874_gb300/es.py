@@ -62,6 +62,8 @@ def _load():
                 "es_state_set": ([vp, vp], c_int),
                 "es_run": ([vp, c_int, c_double, vp, c_int, vp], c_int),
                 "es_superpose": ([vp, c_int, c_int, c_int, vp, vp, vp, c_int, c_double, c_int, vp, vp], c_int),
+                "es_superpose_noalloc": ([vp, c_int, c_int, c_int, vp, vp, vp, c_int, c_double, c_int, vp, vp],
+                                         c_int),
                 "es_seabed_receivers": ([vp, c_int, c_int, pi], c_int),
                 "es_derivative": ([vp, c_int, c_int, c_int, c_int, c_double, c_int, vp, vp], c_int),
                 "es_last_step_kernel_ms": ([vp, ctypes.POINTER(ctypes.c_float), c_int], c_int),
@@ -83,7 +85,7 @@ def exported_symbols():
     return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream",
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_force",
             "es_source_clear", "es_state_reset", "es_state_get", "es_state_set", "es_run",
-            "es_superpose", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
+            "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
             "es_kernels_per_step", "es_model_destroy", "es_status_string", "es_last_error"]
 
 
@@ -147,6 +149,19 @@ def es_superpose(traces, src_of_event, amps, t0s, dt, n_out, gather=None, stream
     gp, gk = _ptr(gather, np.float32)
     _check(lib.es_superpose(tp, n_src, n_rcv, nt, ep, ap, t0p, n_ev, float(dt), int(n_out), gp,
                             _stream_handle(stream)), "es_superpose")
+    return gather
+
+
+def es_superpose_noalloc(traces, src_of_event, amps, t0s, dt, n_out, gather, stream=None):
+    """es_superpose for callers that cannot allocate: every array a torch CUDA
+    tensor (gather [4][n_rcv][n_out] preallocated by the caller)."""
+    lib = _load()
+    n_src, four, n_rcv, nt = traces.shape
+    assert four == 4
+    ptrs = [_ptr(a, dt_)[0] for a, dt_ in ((traces, np.float32), (src_of_event, np.int32), (amps, np.float32),
+                                           (t0s, np.float32), (gather, np.float32))]
+    _check(lib.es_superpose_noalloc(ptrs[0], n_src, n_rcv, nt, ptrs[1], ptrs[2], ptrs[3], len(src_of_event),
+                                    float(dt), int(n_out), ptrs[4], _stream_handle(stream)), "es_superpose_noalloc")
     return gather
 
 
