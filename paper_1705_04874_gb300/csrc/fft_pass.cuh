@@ -204,14 +204,21 @@ __device__ __forceinline__ size_t slab_index(int axis, int x, int y, int z, int 
     return (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * sp);
 }
 
-// one cell: apply job J with derivative d at linear index q
-__device__ __forceinline__ void split_update(float* tot, float* slab, size_t si, float P, float inc)
+// Split-field update inside a PML slab: s <- P (P s + inc).  Returns the
+// change of the split, which is the change of the field total.
+__device__ __forceinline__ float split_delta(float* slab, size_t si, float P, float inc)
 {
-    float s = slab[si];
-    float sn = P * (P * s + inc);
-    *tot += sn - s;
+    const float s = slab[si];
+    const float sn = P * (P * s + inc);
     slab[si] = sn;
+    return sn - s;
 }
+
+// Field totals take their increment by a vector reduction in L2 (atomicAdd
+// with the result unused): within one pass every total receives exactly one
+// increment, and passes are stream-ordered, so the result is the plain
+// rounded sum, deterministic, while the epilogue never waits for the old
+// value.
 
 // Epilogue for a pair of x-adjacent cells (x even) at position `pos` along
 // the axis: q = linear index of the first cell, (x, y, z) its coordinates.
@@ -226,38 +233,30 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
     const bool slab = in_slab(pos, p.n, p.L);
     const int S = 2 * p.L + 1;
     if (J.kind == JOB_SINGLE) {
-        float2 c = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
-        float2 t = *reinterpret_cast<float2*>(J.tgt[0] + q);
-        float i0 = dt * c.x * d0, i1 = dt * c.y * d1;
-        if (!slab) {
-            t.x += i0;
-            t.y += i1;
-        } else {
-            float P = __ldg((J.stag ? p.ps : p.pc) + pos);
-            size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
-            split_update(&t.x, J.slab[0], si, P, i0);
-            split_update(&t.y, J.slab[0], si + 1, P, i1);
+        const float2 c = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
+        float2 inc = make_float2(dt * c.x * d0, dt * c.y * d1);
+        if (slab) {
+            const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
+            const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            inc.x = split_delta(J.slab[0], si, P, inc.x);
+            inc.y = split_delta(J.slab[0], si + 1, P, inc.y);
         }
-        *reinterpret_cast<float2*>(J.tgt[0] + q) = t;
+        atomicAdd(reinterpret_cast<float2*>(J.tgt[0] + q), inc);
     } else {
-        float2 lam = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
-        float2 mu = __ldg(reinterpret_cast<const float2*>(J.coef[1] + q));
-        float P = slab ? __ldg(p.pc + pos) : 1.f;
-        size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+        const float2 lam = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
+        const float2 mu = __ldg(reinterpret_cast<const float2*>(J.coef[1] + q));
+        const float P = slab ? __ldg(p.pc + pos) : 1.f;
+        const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             float2 c = lam;
             if (t == J.diag) { c.x += 2.f * mu.x; c.y += 2.f * mu.y; }
-            float2 v = *reinterpret_cast<float2*>(J.tgt[t] + q);
-            float i0 = dt * c.x * d0, i1 = dt * c.y * d1;
-            if (!slab) {
-                v.x += i0;
-                v.y += i1;
-            } else {
-                split_update(&v.x, J.slab[t], si, P, i0);
-                split_update(&v.y, J.slab[t], si + 1, P, i1);
+            float2 inc = make_float2(dt * c.x * d0, dt * c.y * d1);
+            if (slab) {
+                inc.x = split_delta(J.slab[t], si, P, inc.x);
+                inc.y = split_delta(J.slab[t], si + 1, P, inc.y);
             }
-            *reinterpret_cast<float2*>(J.tgt[t] + q) = v;
+            atomicAdd(reinterpret_cast<float2*>(J.tgt[t] + q), inc);
         }
     }
 }
@@ -276,18 +275,17 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
     const size_t srow = (size_t)S * ((size_t)y + (size_t)p.ny * z);
     if (J.kind == JOB_SINGLE) {
         const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
-        const float4 t4 = *reinterpret_cast<const float4*>(J.tgt[0] + q0);
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-        float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+        float iv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int pos = pos0 + e;
-            const float inc = dt * cv[e] * d[e];
-            if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
-            else split_update(&tv[e], J.slab[0], srow + slab_pos(pos, p.n, p.L),
-                              __ldg((J.stag ? p.ps : p.pc) + pos), inc);
+            iv[e] = dt * cv[e] * d[e];
+            if (in_slab(pos, p.n, p.L))
+                iv[e] = split_delta(J.slab[0], srow + slab_pos(pos, p.n, p.L), __ldg((J.stag ? p.ps : p.pc) + pos),
+                                    iv[e]);
         }
-        *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+        atomicAdd(reinterpret_cast<float4*>(J.tgt[0] + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
     } else {
         const float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
         const float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
@@ -295,17 +293,16 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
         const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            const float4 t4 = *reinterpret_cast<const float4*>(J.tgt[t] + q0);
-            float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+            float iv[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int pos = pos0 + e;
                 const float cc = lv[e] + (t == J.diag ? 2.f * mv[e] : 0.f);
-                const float inc = dt * cc * d[e];
-                if (!in_slab(pos, p.n, p.L)) tv[e] += inc;
-                else split_update(&tv[e], J.slab[t], srow + slab_pos(pos, p.n, p.L), __ldg(p.pc + pos), inc);
+                iv[e] = dt * cc * d[e];
+                if (in_slab(pos, p.n, p.L))
+                    iv[e] = split_delta(J.slab[t], srow + slab_pos(pos, p.n, p.L), __ldg(p.pc + pos), iv[e]);
             }
-            *reinterpret_cast<float4*>(J.tgt[t] + q0) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            atomicAdd(reinterpret_cast<float4*>(J.tgt[t] + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
         }
     }
 }
@@ -398,6 +395,12 @@ __host__ __device__ constexpr int pass_min_blocks()
 template <int RA, int RB, int CPAD>
 __host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * ((size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
 
+// warm L2 with a 128-byte line the epilogue will read (no registers held)
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int N>
 __device__ __forceinline__ void load_tables(const PassParams& p, float2* s_tw, float2* s_hp, float2* s_hm, int tid,
                                             int nthreads)
@@ -445,6 +448,12 @@ pass_strided(const __grid_constant__ PassParams p)
     for (int r = 0; r < RA; ++r)
         a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + base + (size_t)(j + r * BA) * est))
                      : make_float2(0.f, 0.f);
+    // coefficient rows of this tile (128 bytes each) into L2 for the epilogue
+    if (tid < N && J.coef[0] && tx * 2 * CP < p.nx) {
+        const size_t row = base - 2 * c + (size_t)tid * est;
+        prefetch_l2(J.coef[0] + row);
+        if (J.coef[1]) prefetch_l2(J.coef[1] + row);
+    }
     load_tables<N>(p, s_tw, s_hp, s_hm, tid, T * CP);
     Dft<RA>::run(a);
     C::stageA_store(a, buf, j, c);
@@ -490,6 +499,15 @@ pass_x(const __grid_constant__ PassParams p)
     // chunk it -> line r = (it / 4) % 32, x = 4 (4 (it / 128) + it % 4): a warp
     // covers 8 lines x 64 contiguous bytes, and its shared stores hit 32 banks
     float* bf = reinterpret_cast<float*>(buf);
+    // the tile's coefficient lines (contiguous, N lines of 128 bytes) into L2
+    if (J.coef[0] && tid < N) {
+        const size_t off = (size_t)line0 * N + (size_t)tid * 32;
+        if (off < (size_t)nlines * N) {
+            prefetch_l2(J.coef[0] + off);
+            if (J.coef[1]) prefetch_l2(J.coef[1] + off);
+        }
+    }
+#pragma unroll
     for (int it = tid; it < ITEMS; it += NT) {
         const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
         const int xx = (hi * 4 + lo) * 4;
@@ -522,6 +540,7 @@ pass_x(const __grid_constant__ PassParams p)
 #pragma unroll
     for (int q = 0; q < RA; ++q) buf[(j + q * BA) * CPAD + c] = a[q];
     __syncthreads();
+#pragma unroll 4
     for (int it = tid; it < ITEMS; it += NT) {
         const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
         const int xx = (hi * 4 + lo) * 4;
