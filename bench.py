@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--nt", type=int, default=0, help="override time steps per es_run (diagnostics)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-nt", type=int, default=200, help="time steps of the batched measurement")
     args = ap.parse_args()
     w = workload(args.workload)
     if args.nt:
@@ -323,6 +325,9 @@ def main():
 
     if not args.no_e2e and rank == 0:
         line["e2e"] = e2e(es, w, inp, stream)
+    if not args.no_batched and rank == 0:
+        m.close()
+        line["batched"] = measure_batched(es, args.batched_nt, 2, stream)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         v, el, cores = oracle_sample(w, inp, 3)
         line["cpu_baseline"] = {"value": v, "unit": "Mcell-steps/s", "cores": cores, "kind": "oracle",
@@ -333,6 +338,70 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_batched(es, nt, reps, stream):
+    """Batched workload: 64 sources (uniform in the reservoir box, random
+    double couples) on the 128^3 marine model plus 16 on a 96^3 and 8 on a
+    160^3 model, all advanced in one graph (one branch per model); the plain
+    rate is one source per es_run on the 128^3 model."""
+    import torch
+    specs = [(128, 10, 64), (96, 8, 16), (160, 10, 8)]
+    models, rcvs, dts, cells = [], [], [], 0.0
+    for i, (n, pml, nb) in enumerate(specs):
+        rho, cp, cs = synth.marine_model(n, seed=1)
+        dt = 0.3 * 10.0 / float(cp.max())
+        rng = synth.SplitMix64(40 + i)
+        box = synth.reservoir_box((n, n, n), pml)
+        pos = synth.random_positions(rng, box, nb)
+        mts = np.array([synth.random_dc(rng) for _ in range(nb)])
+        wav = np.stack([synth.ricker(nt, dt, 30.0)] * nb)
+        m = es.Model(rho, cp, cs, dx=10.0, pml=pml, stream=stream)
+        rcv = m.seabed_receivers(32, 32)
+        m.batch_set(pos, mts, wav)
+        models.append(m)
+        rcvs.append(torch.from_numpy(rcv).cuda())
+        dts.append(dt)
+        cells += float(n) ** 3 * nb * nt
+    outs = [torch.empty((m.nsim, 4, r.shape[0], nt), device="cuda") for m, r in zip(models, rcvs)]
+
+    def group():
+        for m in models:
+            m.state_reset()
+        es.es_run_group(models, nt, dts, rcvs, outs)
+
+    group()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        group()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # plain: one source at a time on the 128^3 model
+    m0 = models[0]
+    rho, cp, cs = synth.marine_model(128, seed=1)
+    single = es.Model(rho, cp, cs, dx=10.0, pml=10, stream=stream)
+    single.source_set((64, 64, 42), synth.double_couple_sdr(30, 60, 90), torch.from_numpy(
+        synth.ricker(nt, dts[0], 30.0)).cuda())
+    tr = torch.empty((4, rcvs[0].shape[0], nt), device="cuda")
+    single.run(nt, dts[0], rcvs[0], tr)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        single.state_reset()
+        single.run(nt, dts[0], rcvs[0], tr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / reps
+    plain = 128.0 ** 3 * nt / (ms_plain * 1e-3) / 1e6
+    value = cells / (ms * 1e-3) / 1e6
+    for m in models + [single]:
+        m.close()
+    return {"value": round(value, 1), "unit": "Mcell-steps/s", "plain_value": round(plain, 1),
+            "speedup_vs_plain": round(value / plain, 3), "time_steps": nt, "ms_per_run": round(ms, 2),
+            "workload": "64 sources on 128^3 + 16 on 96^3 + 8 on 160^3 marine models, one graph, 32x32 receivers"}
 
 
 def e2e(es, w, inp, stream):

@@ -20,9 +20,9 @@
  *   default stream); a call that returns ES_OK into a host buffer has
  *   finished; into a device buffer, it is complete in stream order.
  * - A model is not thread-safe: one thread at a time per model.
- * - Axis lengths must factor as R1 * R2 with R1, R2 in {3,4,5,6,8,10,12,16}
- *   in the supported list (16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192,
- *   256); nx must be one of them too.  Anything else is ES_ERR_SIZE.
+ * - Every axis length must be one of 16, 32, 48, 64, 80, 96, 128, 160, 192,
+ *   256 (two-stage FFT plans R1 x R2 with R1, R2 in {4,5,6,8,12,16});
+ *   anything else is ES_ERR_SIZE.
  */
 #ifndef ES_H
 #define ES_H
@@ -93,6 +93,18 @@ int es_source_add_force(es_model* m, const int pos[3], const double f[3], const 
 /* Removes every source. */
 int es_source_clear(es_model* m);
 
+/* Batched runs of independent sources on one model (the paper runs thousands
+ * of single-source simulations on the same velocity model, Sec. III-A):
+ * the model then holds nb simulations that share its material arrays, each
+ * driven by one moment-tensor point source -- simulation b by pos[3b..3b+2],
+ * mt[6b..6b+5] (as in es_source_set) and wavelet
+ * wavelets[b nw .. b nw + nw - 1].  Replaces every source, resets the state
+ * and, when nb changes, reallocates the fields (9 nb nx ny nz floats plus
+ * slabs).  es_run then advances all nb simulations in the same kernel
+ * launches and writes traces as [nb][4][n_rcv][nt]; es_state_get/set use
+ * [nb][9][nz][ny][nx].  Arrays host or device.  nb = 1 is the plain model. */
+int es_batch_set(es_model* m, int nb, const int* pos, const double* mt, const float* wavelets, int nw);
+
 /* Sets every field to zero (the state before the first step). */
 int es_state_reset(es_model* m);
 
@@ -113,6 +125,15 @@ int es_state_set(es_model* m, const float* fields);
  * device; n_rcv may be 0 (traces then unused).  The state carries over to
  * the next call (call es_state_reset for a fresh run). */
 int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces);
+
+/* Runs nt steps of nmod models together, as es_run does for each (models[i]
+ * with dts[i], receivers rcvs[i] [n_rcvs[i]][3], traces traces[i]), but
+ * captured into one CUDA graph with one branch per model, so models of
+ * different grid sizes (batched or not) share the GPU concurrently.  The
+ * work is queued on models[0]'s stream.  Models must be distinct.
+ * Per-kernel timings (es_last_step_kernel_ms) are not recorded. */
+int es_run_group(int nmod, es_model* const* models, int nt, const double* dts, const int* const* rcvs,
+                 const int* n_rcvs, float* const* traces);
 
 /* Superposition of single-event traces (Sec. IV): for every event e,
  * k_e = floor(t0s[e] / dt + 1/2) (computed in FP64) and

@@ -10,7 +10,7 @@ namespace es {
 // fixed order.  The step counter lives on the device so that one captured
 // step can be replayed: the kernel that runs last in a step (`advance`)
 // publishes the step index to `cur` for the recorder and increments it.
-__global__ void inject_kernel(float* const* fields, const SourceDev* src, int nsrc, int kind,
+__global__ void inject_kernel(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
                               int* counter, int* cur, int advance)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -19,14 +19,15 @@ __global__ void inject_kernel(float* const* fields, const SourceDev* src, int ns
         const SourceDev s = src[e];
         if (s.kind != kind || n >= s.nw) continue;
         const float w = s.w[n];
+        const long long q = (long long)s.sim * fstride + s.cell;
         if (kind == 0) {
             // moment tensor: stress component i gains M_i w[n] (Mxx Myy Mzz Mxy Mxz Myz)
             for (int c = 0; c < 6; ++c)
-                if (s.m[c] != 0.f) fields[SXX + c][s.cell] += s.m[c] * w;
+                if (s.m[c] != 0.f) fields[SXX + c][q] += s.m[c] * w;
         } else {
             // point force: m[c] = dt f_c / (rho_c dx dy dz), folded on the host
             for (int c = 0; c < 3; ++c)
-                if (s.m[c] != 0.f) fields[VX + c][s.cell] += s.m[c] * w;
+                if (s.m[c] != 0.f) fields[VX + c][q] += s.m[c] * w;
         }
     }
     if (advance) {
@@ -35,21 +36,23 @@ __global__ void inject_kernel(float* const* fields, const SourceDev* src, int ns
     }
 }
 
-cudaError_t launch_inject(float* const* fields, const SourceDev* src, int nsrc, int kind, int* counter,
-                          int* cur, int advance, cudaStream_t st)
+cudaError_t launch_inject(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
+                          int* counter, int* cur, int advance, cudaStream_t st)
 {
-    inject_kernel<<<1, 32, 0, st>>>(fields, src, nsrc, kind, counter, cur, advance);
+    inject_kernel<<<1, 32, 0, st>>>(fields, fstride, src, nsrc, kind, counter, cur, advance);
     return cudaGetLastError();
 }
 
-// rec[n - start][c][r]: sample n of component c (p, vx, vy, vz) at receiver r
-__global__ void record_kernel(float* const* fields, const long long* rcv_cell, int n_rcv, const int* cur,
-                              long long start, float* rec)
+// rec[n - start][sim][c][r]: sample n of component c (p, vx, vy, vz) of
+// simulation sim at receiver r
+__global__ void record_kernel(float* const* fields, long long fstride, int nsim, const long long* rcv_cell, int n_rcv,
+                              const int* cur, long long start, float* rec)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rcv) return;
-    const long long q = rcv_cell[r];
-    const size_t row = (size_t)(*cur - start) * 4 * n_rcv;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rcv * nsim) return;
+    const int r = i % n_rcv, sim = i / n_rcv;
+    const long long q = (long long)sim * fstride + rcv_cell[r];
+    const size_t row = ((size_t)(*cur - start) * nsim + sim) * 4 * n_rcv;
     const float s = fields[SXX][q] + fields[SYY][q] + fields[SZZ][q];
     rec[row + r] = -s / 3.f;  // Eq. (3)
     rec[row + n_rcv + r] = fields[VX][q];
@@ -57,15 +60,16 @@ __global__ void record_kernel(float* const* fields, const long long* rcv_cell, i
     rec[row + 3 * (size_t)n_rcv + r] = fields[VZ][q];
 }
 
-cudaError_t launch_record(float* const* fields, const long long* rcv_cell, int n_rcv, const int* cur,
-                          long long start, float* rec, cudaStream_t st)
+cudaError_t launch_record(float* const* fields, long long fstride, int nsim, const long long* rcv_cell, int n_rcv,
+                          const int* cur, long long start, float* rec, cudaStream_t st)
 {
     if (n_rcv <= 0) return cudaSuccess;
-    record_kernel<<<(n_rcv + 127) / 128, 128, 0, st>>>(fields, rcv_cell, n_rcv, cur, start, rec);
+    const int n = n_rcv * nsim;
+    record_kernel<<<(n + 127) / 128, 128, 0, st>>>(fields, fstride, nsim, rcv_cell, n_rcv, cur, start, rec);
     return cudaGetLastError();
 }
 
-// [nt][4 n_rcv] -> [4 n_rcv][nt] through a 32 x 32 shared tile
+// [rows][cols] -> [cols][rows] through a 32 x 32 shared tile
 __global__ void transpose_kernel(const float* in, int rows, int cols, float* out)
 {
     __shared__ float tile[32][33];
@@ -81,9 +85,8 @@ __global__ void transpose_kernel(const float* in, int rows, int cols, float* out
     }
 }
 
-cudaError_t launch_transpose_traces(const float* rec, int nt, int n_rcv, float* out, cudaStream_t st)
+cudaError_t launch_transpose_traces(const float* rec, int nt, int cols, float* out, cudaStream_t st)
 {
-    const int cols = 4 * n_rcv;
     dim3 grid((cols + 31) / 32, (nt + 31) / 32), block(32, 8);
     transpose_kernel<<<grid, block, 0, st>>>(rec, nt, cols, out);
     return cudaGetLastError();

@@ -100,6 +100,7 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
 
 struct Src {
     int kind;
+    int sim;
     int pos[3];
     double m[6];
     float* d_w;
@@ -119,7 +120,9 @@ struct es_model {
     cudaStream_t stream = nullptr;
     std::vector<float> rho, cs;  // host copies (seabed rule, force scaling)
     float cp_max = 0.f;
-    char* pool = nullptr;
+    char* pool = nullptr;   // materials, tables, counters
+    int nsim = 1;           // independent simulations sharing the materials
+    char* fpool = nullptr;  // field totals and slab splits, [field][sim][cell]
     float* f[NFIELD] = {};
     float* slab[3][NFIELD] = {};
     float* mat[NMAT] = {};
@@ -171,6 +174,7 @@ int upload_sources(es_model* m, double dt)
         const Src& s = m->srcs[e];
         SourceDev& d = h[e];
         d.kind = s.kind;
+        d.sim = s.sim;
         d.cell = (long long)s.pos[0] + (long long)m->nx * ((long long)s.pos[1] + (long long)m->ny * s.pos[2]);
         d.w = s.d_w;
         d.nw = s.nw;
@@ -220,6 +224,9 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.ps = m->ps[axis];
     p.L = m->L;
     p.dt = dt;
+    p.nsim = m->nsim;
+    p.fstride = (long long)m->ncell;
+    p.sstride = (long long)slab_count(m, axis);
     auto single = [&](PassJob& J, int src, int sign, int tgt, int coef) {
         J.src = m->f[src];
         J.kind = JOB_SINGLE;
@@ -282,7 +289,8 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
     }
     if (has_force) {
         mark(true);
-        CK(launch_inject(m->d_fields, m->d_src, (int)m->srcs.size(), 1, m->d_int, m->d_int + 1, 0, st));
+        CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 1, m->d_int, m->d_int + 1, 0,
+                         st));
         mark(false);
         ++k;
     }
@@ -294,12 +302,14 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         ++k;
     }
     mark(true);
-    CK(launch_inject(m->d_fields, m->d_src, (int)m->srcs.size(), 0, m->d_int, m->d_int + 1, 1, st));
+    CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 0, m->d_int, m->d_int + 1, 1,
+                     st));
     mark(false);
     ++k;
     if (n_rcv > 0) {
         mark(true);
-        CK(launch_record(m->d_fields, m->d_rcv, n_rcv, m->d_int + 1, start, m->d_rec, st));
+        CK(launch_record(m->d_fields, (long long)m->ncell, m->nsim, m->d_rcv, n_rcv, m->d_int + 1, start, m->d_rec,
+                         st));
         mark(false);
         ++k;
     }
@@ -330,6 +340,33 @@ int capture(es_model* m, int steps, float dt, int n_rcv, long long start, bool t
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     m->n_last = nk;
+    return ES_OK;
+}
+
+// (Re)allocates the field totals and slab splits for nsim simulations:
+// field f of simulation k at f[f] + k ncell, its split along axis a at
+// slab[a][f] + k slab_count(a).
+int alloc_fields(es_model* m, int nsim)
+{
+    const size_t A = 256;
+    auto up = [&](size_t b) { return (b + A - 1) / A * A; };
+    size_t bytes = up(m->ncell * 4 * (size_t)nsim) * NFIELD;
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f)
+            if (m->L > 0 && has_split(f, a)) bytes += up(slab_count(m, a) * 4 * (size_t)nsim);
+    char* pool = nullptr;
+    cudaError_t e = cudaMalloc(&pool, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fields)");
+    cudaFree(m->fpool);
+    m->fpool = pool;
+    m->nsim = nsim;
+    char* cur = pool;
+    auto take = [&](size_t b) { char* p = cur; cur += up(b); return p; };
+    for (int f = 0; f < NFIELD; ++f) m->f[f] = (float*)take(m->ncell * 4 * (size_t)nsim);
+    for (int a = 0; a < 3; ++a)
+        for (int f = 0; f < NFIELD; ++f)
+            m->slab[a][f] = (m->L > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4 * (size_t)nsim) : nullptr;
+    CK(cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice));
     return ES_OK;
 }
 
@@ -370,6 +407,7 @@ void es_model_destroy(es_model* m)
     cudaFree(m->d_out);
     cudaFree(m->d_rcv);
     cudaFree(m->pool);
+    cudaFree(m->fpool);
     for (auto& e : m->ev)
         if (e) cudaEventDestroy(e);
     delete m;
@@ -413,10 +451,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     // one pool: fields, materials, slabs, per-axis tables, counters, pointer table
     const size_t A = 256;
     auto up = [&](size_t b) { return (b + A - 1) / A * A; };
-    size_t bytes = up(n * 4) * (NFIELD + NMAT);
-    for (int a = 0; a < 3; ++a)
-        for (int f = 0; f < NFIELD; ++f)
-            if (pml > 0 && has_split(f, a)) bytes += up(slab_count(m, a) * 4);
+    size_t bytes = up(n * 4) * NMAT;
     for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 2 * up(axis_len(m, a) * 4);
     bytes += up(16) + up(NFIELD * sizeof(float*));
     cudaError_t e = cudaMalloc(&m->pool, bytes);
@@ -426,11 +461,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     }
     char* cur = m->pool;
     auto take = [&](size_t b) { char* p = cur; cur += up(b); return p; };
-    for (int f = 0; f < NFIELD; ++f) m->f[f] = (float*)take(n * 4);
     for (int k = 0; k < NMAT; ++k) m->mat[k] = (float*)take(n * 4);
-    for (int a = 0; a < 3; ++a)
-        for (int f = 0; f < NFIELD; ++f)
-            m->slab[a][f] = (pml > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4) : nullptr;
     for (int a = 0; a < 3; ++a) {
         m->tw[a] = (float2*)take(axis_len(m, a) * 8);
         m->hp[a] = (float2*)take(axis_len(m, a) * 8);
@@ -482,12 +513,16 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice);
     for (int k = 0; k < 2 * KPS_MAX && e == cudaSuccess; ++k) e = cudaEventCreate(&m->ev[k]);
     if (e != cudaSuccess) {
         int r = cuda_fail(e, "es_model_create");
         es_model_destroy(m);
         return r;
+    }
+    rc = alloc_fields(m, 1);
+    if (rc != ES_OK) {
+        es_model_destroy(m);
+        return rc;
     }
     rc = es_state_reset(m);
     if (rc != ES_OK) {
@@ -547,6 +582,7 @@ static int add_source(es_model* m, int kind, const int pos[3], const double* v, 
     if (rc != ES_OK) return rc;
     Src s;
     s.kind = kind;
+    s.sim = 0;
     std::memcpy(s.pos, pos, sizeof s.pos);
     for (int c = 0; c < 6; ++c) s.m[c] = c < nv ? v[c] : 0.0;
     s.nw = nw;
@@ -561,6 +597,45 @@ static int add_source(es_model* m, int kind, const int pos[3], const double* v, 
     }
     m->srcs.push_back(s);
     return ES_OK;
+}
+
+int es_batch_set(es_model* m, int nb, const int* pos, const double* mt, const float* wavelets, int nw)
+{
+    if (!m || nb < 1 || !pos || !mt || nw < 0 || (nw > 0 && !wavelets)) return ES_ERR_ARG;
+    std::vector<int> hp;
+    std::vector<double> hm;
+    std::vector<float> hw;
+    int rc;
+    if ((rc = fetch(pos, (size_t)nb * 3, hp, m->stream)) != ES_OK) return rc;
+    if ((rc = fetch(mt, (size_t)nb * 6, hm, m->stream)) != ES_OK) return rc;
+    if ((rc = fetch(wavelets, (size_t)nb * nw, hw, m->stream)) != ES_OK) return rc;
+    for (int b = 0; b < nb; ++b) {
+        for (int a = 0; a < 3; ++a)
+            if (hp[3 * b + a] < m->L || hp[3 * b + a] > axis_len(m, a) - 2 - m->L) return ES_ERR_ARG;
+        for (int c = 0; c < 6; ++c)
+            if (!std::isfinite(hm[6 * b + c])) return ES_ERR_ARG;
+    }
+    if ((rc = es_source_clear(m)) != ES_OK) return rc;
+    if (nb != m->nsim && (rc = alloc_fields(m, nb)) != ES_OK) return rc;
+    for (int b = 0; b < nb; ++b) {
+        Src s;
+        s.kind = 0;
+        s.sim = b;
+        std::memcpy(s.pos, &hp[3 * b], sizeof s.pos);
+        for (int c = 0; c < 6; ++c) s.m[c] = hm[6 * b + c];
+        s.nw = nw;
+        s.d_w = nullptr;
+        if (nw > 0) {
+            CK(cudaMalloc(&s.d_w, sizeof(float) * nw));
+            cudaError_t e = cudaMemcpy(s.d_w, &hw[(size_t)b * nw], sizeof(float) * nw, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(s.d_w);
+                return cuda_fail(e, "cudaMemcpy(wavelet)");
+            }
+        }
+        m->srcs.push_back(s);
+    }
+    return es_state_reset(m);
 }
 
 int es_source_clear(es_model* m)
@@ -593,10 +668,11 @@ int es_source_add_force(es_model* m, const int pos[3], const double f[3], const 
 int es_state_reset(es_model* m)
 {
     if (!m) return ES_ERR_ARG;
-    for (int f = 0; f < NFIELD; ++f) CK(cudaMemsetAsync(m->f[f], 0, m->ncell * 4, m->stream));
+    const size_t ns = (size_t)m->nsim;
+    for (int f = 0; f < NFIELD; ++f) CK(cudaMemsetAsync(m->f[f], 0, m->ncell * 4 * ns, m->stream));
     for (int a = 0; a < 3; ++a)
         for (int f = 0; f < NFIELD; ++f)
-            if (m->slab[a][f]) CK(cudaMemsetAsync(m->slab[a][f], 0, slab_count(m, a) * 4, m->stream));
+            if (m->slab[a][f]) CK(cudaMemsetAsync(m->slab[a][f], 0, slab_count(m, a) * 4 * ns, m->stream));
     CK(cudaMemsetAsync(m->d_int, 0, 16, m->stream));
     CK(cudaStreamSynchronize(m->stream));
     m->steps_done = 0;
@@ -607,7 +683,10 @@ int es_state_get(es_model* m, float* fields)
 {
     if (!m || !fields) return ES_ERR_ARG;
     const cudaMemcpyKind k = is_device_ptr(fields) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    for (int f = 0; f < NFIELD; ++f) CK(cudaMemcpyAsync(fields + (size_t)f * m->ncell, m->f[f], m->ncell * 4, k, m->stream));
+    for (int k2 = 0; k2 < m->nsim; ++k2)
+        for (int f = 0; f < NFIELD; ++f)
+            CK(cudaMemcpyAsync(fields + ((size_t)k2 * NFIELD + f) * m->ncell, m->f[f] + (size_t)k2 * m->ncell,
+                               m->ncell * 4, k, m->stream));
     CK(cudaStreamSynchronize(m->stream));
     return ES_OK;
 }
@@ -616,28 +695,35 @@ int es_state_set(es_model* m, const float* fields)
 {
     if (!m || !fields) return ES_ERR_ARG;
     const cudaMemcpyKind k = is_device_ptr(fields) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    for (int f = 0; f < NFIELD; ++f) CK(cudaMemcpyAsync(m->f[f], fields + (size_t)f * m->ncell, m->ncell * 4, k, m->stream));
-    for (int a = 0; a < 3; ++a)
-        for (int f = 0; f < NFIELD; ++f) {
-            if (!m->slab[a][f]) continue;
-            const int first = has_split(f, 0) ? 0 : 1;  // the split carrying the whole value
-            CK(launch_fill_slab(m->f[f], m->slab[a][f], a, m->nx, m->ny, m->nz, m->L, a == first, m->stream));
-        }
+    for (int k2 = 0; k2 < m->nsim; ++k2) {
+        const size_t fo = (size_t)k2 * m->ncell;
+        for (int f = 0; f < NFIELD; ++f)
+            CK(cudaMemcpyAsync(m->f[f] + fo, fields + ((size_t)k2 * NFIELD + f) * m->ncell, m->ncell * 4, k, m->stream));
+        for (int a = 0; a < 3; ++a)
+            for (int f = 0; f < NFIELD; ++f) {
+                if (!m->slab[a][f]) continue;
+                const int first = has_split(f, 0) ? 0 : 1;  // the split carrying the whole value
+                CK(launch_fill_slab(m->f[f] + fo, m->slab[a][f] + (size_t)k2 * slab_count(m, a), a, m->nx, m->ny,
+                                    m->nz, m->L, a == first, m->stream));
+            }
+    }
     CK(cudaStreamSynchronize(m->stream));
     return ES_OK;
 }
 
-int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces)
+// Validation and per-run set-up of es_run: receivers, buffers, PML factors
+// for dt, sources.  dt <= 0 is replaced by the default.
+static int run_prepare(es_model* m, int nt, double* pdt, const int* rcv, int n_rcv, float* traces)
 {
-    int rc = run_checked_args(m, nt, dt, n_rcv);
+    int rc = run_checked_args(m, nt, *pdt, n_rcv);
     if (rc != ES_OK) return rc;
+    double& dt = *pdt;
     cudaGetLastError();  // launch checks below must not see an earlier, unrelated error
     if (n_rcv > 0 && (!rcv || !traces)) return ES_ERR_ARG;
     if (!(dt > 0)) es_model_default_dt(m, &dt);
     // stability of the staggered pseudo-spectral leapfrog: c dt |kappa_max| <= 2
     const double s = std::sqrt(1.0 / (m->d[0] * m->d[0]) + 1.0 / (m->d[1] * m->d[1]) + 1.0 / (m->d[2] * m->d[2]));
     if ((double)m->cp_max * dt * s > 2.0 / 3.14159265358979323846) return ES_ERR_UNSTABLE;
-    if (nt == 0) return ES_OK;
 
     std::vector<int> h_rcv;
     if ((rc = fetch(rcv, (size_t)n_rcv * 3, h_rcv, m->stream)) != ES_OK) return rc;
@@ -654,7 +740,7 @@ int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* tra
         CK(cudaMalloc(&m->d_rcv, sizeof(long long) * n_rcv));
         m->rcv_cap = n_rcv;
     }
-    const size_t rec_n = (size_t)nt * 4 * n_rcv;
+    const size_t rec_n = (size_t)nt * m->nsim * 4 * n_rcv;
     if (rec_n > m->rec_cap) {
         cudaFree(m->d_rec);
         m->d_rec = nullptr;
@@ -686,31 +772,17 @@ int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* tra
         CK(cudaStreamSynchronize(m->stream));
     }
     if ((rc = upload_sources(m, dt)) != ES_OK) return rc;
+    return ES_OK;
+}
 
-    // graphs: K steps, 1 step, 1 step with per-kernel events (the last step)
-    const long long start = m->steps_done;
-    const int K = 16;
-    cudaGraphExec_t gK = nullptr, g1 = nullptr, gT = nullptr;
-    const int body = nt - 1;
-    rc = ES_OK;
-    if (body >= K) rc = capture(m, K, (float)dt, n_rcv, start, false, &gK);
-    if (rc == ES_OK && body % K) rc = capture(m, 1, (float)dt, n_rcv, start, false, &g1);
-    if (rc == ES_OK) rc = capture(m, 1, (float)dt, n_rcv, start, true, &gT);
-    cudaError_t e = cudaSuccess;
-    if (rc == ES_OK) {
-        for (int i = 0; i < body / K && e == cudaSuccess; ++i) e = cudaGraphLaunch(gK, m->stream);
-        for (int i = 0; i < body % K && e == cudaSuccess; ++i) e = cudaGraphLaunch(g1, m->stream);
-        if (e == cudaSuccess) e = cudaGraphLaunch(gT, m->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(m->d_int + 2, 0, 4, m->stream);
-        if (e == cudaSuccess) e = launch_nonfinite(m->d_fields, m->ncell, m->d_int + 2, m->stream);
-    }
-    if (gK) cudaGraphExecDestroy(gK);
-    if (g1) cudaGraphExecDestroy(g1);
-    if (gT) cudaGraphExecDestroy(gT);
-    if (rc != ES_OK) return rc;
-    if (e != cudaSuccess) return cuda_fail(e, "es_run launch");
+// After the steps of a run are queued on st: non-finite check, traces out,
+// completion.
+static int run_finish(es_model* m, int nt, int n_rcv, float* traces, cudaStream_t st)
+{
+    CK(cudaMemsetAsync(m->d_int + 2, 0, 4, st));
+    CK(launch_nonfinite(m->d_fields, m->ncell * m->nsim, m->d_int + 2, st));
     m->steps_done += nt;
-
+    const size_t rec_n = (size_t)nt * m->nsim * 4 * n_rcv;
     if (n_rcv > 0) {
         const bool dev_out = is_device_ptr(traces);
         float* dst = traces;
@@ -724,14 +796,125 @@ int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* tra
             }
             dst = m->d_out;
         }
-        CK(launch_transpose_traces(m->d_rec, nt, n_rcv, dst, m->stream));
-        if (!dev_out) CK(cudaMemcpyAsync(traces, dst, rec_n * 4, cudaMemcpyDeviceToHost, m->stream));
+        CK(launch_transpose_traces(m->d_rec, nt, m->nsim * 4 * n_rcv, dst, st));
+        if (!dev_out) CK(cudaMemcpyAsync(traces, dst, rec_n * 4, cudaMemcpyDeviceToHost, st));
     }
     int flag = 0;
-    CK(cudaMemcpyAsync(&flag, m->d_int + 2, 4, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    for (int k = 0; k < m->n_last; ++k) CK(cudaEventElapsedTime(&m->last_ms[k], m->ev[2 * k], m->ev[2 * k + 1]));
+    CK(cudaMemcpyAsync(&flag, m->d_int + 2, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return flag ? ES_ERR_UNSTABLE : ES_OK;
+}
+
+int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces)
+{
+    int rc = run_prepare(m, nt, &dt, rcv, n_rcv, traces);
+    if (rc != ES_OK || nt == 0) return rc;
+    // graphs: K steps, 1 step, 1 step with per-kernel events (the last step)
+    const long long start = m->steps_done;
+    const int K = 16;
+    cudaGraphExec_t gK = nullptr, g1 = nullptr, gT = nullptr;
+    const int body = nt - 1;
+    if (body >= K) rc = capture(m, K, (float)dt, n_rcv, start, false, &gK);
+    if (rc == ES_OK && body % K) rc = capture(m, 1, (float)dt, n_rcv, start, false, &g1);
+    if (rc == ES_OK) rc = capture(m, 1, (float)dt, n_rcv, start, true, &gT);
+    cudaError_t e = cudaSuccess;
+    if (rc == ES_OK) {
+        for (int i = 0; i < body / K && e == cudaSuccess; ++i) e = cudaGraphLaunch(gK, m->stream);
+        for (int i = 0; i < body % K && e == cudaSuccess; ++i) e = cudaGraphLaunch(g1, m->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gT, m->stream);
+    }
+    if (gK) cudaGraphExecDestroy(gK);
+    if (g1) cudaGraphExecDestroy(g1);
+    if (gT) cudaGraphExecDestroy(gT);
+    if (rc != ES_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "es_run launch");
+    rc = run_finish(m, nt, n_rcv, traces, m->stream);
+    if (rc == ES_OK || rc == ES_ERR_UNSTABLE)
+        for (int k = 0; k < m->n_last; ++k) CK(cudaEventElapsedTime(&m->last_ms[k], m->ev[2 * k], m->ev[2 * k + 1]));
+    return rc;
+}
+
+// One graph holding `steps` time steps of every model, each model on its own
+// branch forked from and joined back to the capture stream.
+static int capture_group(es_model* const* ms, int nmod, int steps, const double* dts, const int* n_rcv,
+                         const long long* starts, cudaGraphExec_t* exec)
+{
+    cudaStream_t root = nullptr;
+    std::vector<cudaStream_t> br(nmod, nullptr);
+    std::vector<cudaEvent_t> join(nmod, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t g = nullptr;
+    int rc = ES_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < nmod && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(fork, root);
+        for (int i = 0; i < nmod && rc == ES_OK; ++i) {
+            cudaStreamWaitEvent(br[i], fork, 0);
+            int nk = 0;
+            for (int s = 0; s < steps && rc == ES_OK; ++s)
+                rc = enqueue_step(ms[i], (float)dts[i], n_rcv[i], starts[i], br[i], nullptr, &nk);
+            cudaEventRecord(join[i], br[i]);
+            cudaStreamWaitEvent(root, join[i], 0);
+        }
+        e = cudaStreamEndCapture(root, &g);
+        if (e == cudaSuccess && rc == ES_OK) e = cudaGraphInstantiate(exec, g, 0);
+    }
+    if (g) cudaGraphDestroy(g);
+    for (int i = 0; i < nmod; ++i) {
+        if (br[i]) cudaStreamDestroy(br[i]);
+        if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (root) cudaStreamDestroy(root);
+    if (rc != ES_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "capture_group");
+    return ES_OK;
+}
+
+int es_run_group(int nmod, es_model* const* models, int nt, const double* dts, const int* const* rcvs,
+                 const int* n_rcvs, float* const* traces)
+{
+    if (nmod < 1 || !models || !dts || !rcvs || !n_rcvs || !traces || nt < 0) return ES_ERR_ARG;
+    for (int i = 0; i < nmod; ++i) {
+        if (!models[i]) return ES_ERR_ARG;
+        for (int k = 0; k < i; ++k)
+            if (models[k] == models[i]) return ES_ERR_ARG;
+    }
+    std::vector<double> dt(dts, dts + nmod);
+    std::vector<long long> starts(nmod);
+    for (int i = 0; i < nmod; ++i) {
+        int rc = run_prepare(models[i], nt, &dt[i], rcvs[i], n_rcvs[i], traces[i]);
+        if (rc != ES_OK) return rc;
+        starts[i] = models[i]->steps_done;
+    }
+    if (nt == 0) return ES_OK;
+    cudaStream_t st = models[0]->stream;
+    const int K = 16;
+    cudaGraphExec_t gK = nullptr, g1 = nullptr;
+    int rc = ES_OK;
+    if (nt >= K) rc = capture_group(models, nmod, K, dt.data(), n_rcvs, starts.data(), &gK);
+    if (rc == ES_OK && nt % K) rc = capture_group(models, nmod, 1, dt.data(), n_rcvs, starts.data(), &g1);
+    cudaError_t e = cudaSuccess;
+    if (rc == ES_OK) {
+        for (int i = 0; i < nt / K && e == cudaSuccess; ++i) e = cudaGraphLaunch(gK, st);
+        for (int i = 0; i < nt % K && e == cudaSuccess; ++i) e = cudaGraphLaunch(g1, st);
+    }
+    if (gK) cudaGraphExecDestroy(gK);
+    if (g1) cudaGraphExecDestroy(g1);
+    if (rc != ES_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "es_run_group launch");
+    int worst = ES_OK;
+    for (int i = 0; i < nmod; ++i) {
+        const int r = run_finish(models[i], nt, n_rcvs[i], traces[i], st);
+        if (r != ES_OK && worst == ES_OK) worst = r;
+    }
+    return worst;
 }
 
 int es_last_step_kernel_ms(es_model* m, float* ms, int n)
@@ -846,6 +1029,7 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
         p.axis = axis;
         p.n = n;
         p.njobs = 1;
+        p.nsim = 1;
         p.tw = tab;
         p.hp = tab + n;
         p.hm = tab + 2 * n;

@@ -43,6 +43,9 @@ struct PassParams {
     const float* ps;      // PML factors at half indices along the axis
     int L;                // PML cells per face (slab width 2L+1, none if 0)
     float dt;
+    int nsim;             // independent simulations sharing the materials
+    long long fstride;    // elements between consecutive simulations' field arrays
+    long long sstride;    // elements between consecutive simulations' slab arrays (this axis)
 };
 
 // Plan of the two-stage FFT for an axis length (0 if unsupported).
@@ -55,18 +58,20 @@ cudaError_t prepare_pass_kernels();
 // ---- auxiliary kernels (aux_kernels.cu) ----
 struct SourceDev {
     int kind;            // 0 moment, 1 force
+    int sim;             // simulation the source belongs to
     long long cell;      // linear index
     float m[6];          // moment (Mxx Myy Mzz Mxy Mxz Myz) or force scale per component
     const float* w;      // wavelet samples (device)
     int nw;
 };
 
-cudaError_t launch_inject(float* const* fields, const SourceDev* src, int nsrc, int kind,
+cudaError_t launch_inject(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
                           int* counter, int* cur, int advance, cudaStream_t st);
-cudaError_t launch_record(float* const* fields, const long long* rcv_cell, int n_rcv,
-                          const int* cur, long long start, float* rec, cudaStream_t st);
-cudaError_t launch_transpose_traces(const float* rec, int nt, int n_rcv, float* out,
-                                    cudaStream_t st);
+// rec[n - start][sim][4][n_rcv]
+cudaError_t launch_record(float* const* fields, long long fstride, int nsim, const long long* rcv_cell,
+                          int n_rcv, const int* cur, long long start, float* rec, cudaStream_t st);
+// [nt][cols] -> [cols][nt]
+cudaError_t launch_transpose_traces(const float* rec, int nt, int cols, float* out, cudaStream_t st);
 cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* ev_src,
                              const float* ev_amp, const int* ev_shift, int n_events, int n_out,
                              float* gather, cudaStream_t st);

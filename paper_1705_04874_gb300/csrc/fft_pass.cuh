@@ -221,12 +221,14 @@ __device__ __forceinline__ float split_delta(float* slab, size_t si, float P, fl
 // value.
 
 // Epilogue for a pair of x-adjacent cells (x even) at position `pos` along
-// the axis: q = linear index of the first cell, (x, y, z) its coordinates.
+// the axis: q = linear index of the first cell, (x, y, z) its coordinates;
+// off / soff = this simulation's offset into the field / slab arrays
+// (materials are shared by all simulations).
 __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob& J, size_t q, int pos,
-                                              int x, int y, int z, float d0, float d1)
+                                              int x, int y, int z, float d0, float d1, size_t off, size_t soff)
 {
     if (J.kind == JOB_STORE) {
-        *reinterpret_cast<float2*>(J.tgt[0] + q) = make_float2(d0, d1);
+        *reinterpret_cast<float2*>(J.tgt[0] + off + q) = make_float2(d0, d1);
         return;
     }
     const float dt = p.dt;
@@ -238,10 +240,10 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
         if (slab) {
             const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
             const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
-            inc.x = split_delta(J.slab[0], si, P, inc.x);
-            inc.y = split_delta(J.slab[0], si + 1, P, inc.y);
+            inc.x = split_delta(J.slab[0], soff + si, P, inc.x);
+            inc.y = split_delta(J.slab[0], soff + si + 1, P, inc.y);
         }
-        atomicAdd(reinterpret_cast<float2*>(J.tgt[0] + q), inc);
+        atomicAdd(reinterpret_cast<float2*>(J.tgt[0] + off + q), inc);
     } else {
         const float2 lam = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
         const float2 mu = __ldg(reinterpret_cast<const float2*>(J.coef[1] + q));
@@ -253,10 +255,10 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
             if (t == J.diag) { c.x += 2.f * mu.x; c.y += 2.f * mu.y; }
             float2 inc = make_float2(dt * c.x * d0, dt * c.y * d1);
             if (slab) {
-                inc.x = split_delta(J.slab[t], si, P, inc.x);
-                inc.y = split_delta(J.slab[t], si + 1, P, inc.y);
+                inc.x = split_delta(J.slab[t], soff + si, P, inc.x);
+                inc.y = split_delta(J.slab[t], soff + si + 1, P, inc.y);
             }
-            atomicAdd(reinterpret_cast<float2*>(J.tgt[t] + q), inc);
+            atomicAdd(reinterpret_cast<float2*>(J.tgt[t] + off + q), inc);
         }
     }
 }
@@ -264,15 +266,15 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
 // Epilogue for 4 x-consecutive cells of one x line (x pass): q0 = linear
 // index of the first, pos0 its x, d[] the derivatives.
 __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob& J, size_t q0, int pos0,
-                                              int y, int z, const float* d)
+                                              int y, int z, const float* d, size_t off, size_t soff)
 {
     if (J.kind == JOB_STORE) {
-        *reinterpret_cast<float4*>(J.tgt[0] + q0) = make_float4(d[0], d[1], d[2], d[3]);
+        *reinterpret_cast<float4*>(J.tgt[0] + off + q0) = make_float4(d[0], d[1], d[2], d[3]);
         return;
     }
     const float dt = p.dt;
     const int S = 2 * p.L + 1;
-    const size_t srow = (size_t)S * ((size_t)y + (size_t)p.ny * z);
+    const size_t srow = soff + (size_t)S * ((size_t)y + (size_t)p.ny * z);
     if (J.kind == JOB_SINGLE) {
         const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -285,7 +287,7 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
                 iv[e] = split_delta(J.slab[0], srow + slab_pos(pos, p.n, p.L), __ldg((J.stag ? p.ps : p.pc) + pos),
                                     iv[e]);
         }
-        atomicAdd(reinterpret_cast<float4*>(J.tgt[0] + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
+        atomicAdd(reinterpret_cast<float4*>(J.tgt[0] + off + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
     } else {
         const float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
         const float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
@@ -302,7 +304,7 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
                 if (in_slab(pos, p.n, p.L))
                     iv[e] = split_delta(J.slab[t], srow + slab_pos(pos, p.n, p.L), __ldg(p.pc + pos), iv[e]);
             }
-            atomicAdd(reinterpret_cast<float4*>(J.tgt[t] + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
+            atomicAdd(reinterpret_cast<float4*>(J.tgt[t] + off + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
         }
     }
 }
@@ -428,8 +430,12 @@ pass_strided(const __grid_constant__ PassParams p)
     const int tid = threadIdx.x;
     const int c = tid % CP, j = tid / CP;
     const PassJob& J = p.job[blockIdx.y];
+    // simulations run fastest in blockIdx.x: the CTAs of one tile are adjacent
+    // and read that tile's material rows through L2
+    const int sim = blockIdx.x % p.nsim, tile = blockIdx.x / p.nsim;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
-    const int tx = blockIdx.x % ntx, outer = blockIdx.x / ntx;
+    const int tx = tile % ntx, outer = tile / ntx;
     const int x = tx * 2 * CP + 2 * c;
     const bool valid = x < p.nx;
     size_t base, est;
@@ -446,7 +452,7 @@ pass_strided(const __grid_constant__ PassParams p)
     float2 a[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r)
-        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + base + (size_t)(j + r * BA) * est))
+        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + off + base + (size_t)(j + r * BA) * est))
                      : make_float2(0.f, 0.f);
     // coefficient rows of this tile (128 bytes each) into L2 for the epilogue
     if (tid < N && J.coef[0] && tx * 2 * CP < p.nx) {
@@ -471,7 +477,7 @@ pass_strided(const __grid_constant__ PassParams p)
     for (int q = 0; q < RA; ++q) {
         const int pos = j + q * BA;
         if (p.axis == 1) y = pos; else z = pos;
-        epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y);
+        epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y, off, soff);
     }
 }
 
@@ -495,7 +501,9 @@ pass_x(const __grid_constant__ PassParams p)
     const int c = tid % CP, j = tid / CP;
     const PassJob& J = p.job[blockIdx.y];
     const int nlines = p.ny * p.nz;
-    const int line0 = blockIdx.x * LINES;
+    const int sim = blockIdx.x % p.nsim;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
+    const int line0 = (blockIdx.x / p.nsim) * LINES;
     // chunk it -> line r = (it / 4) % 32, x = 4 (4 (it / 128) + it % 4): a warp
     // covers 8 lines x 64 contiguous bytes, and its shared stores hit 32 banks
     float* bf = reinterpret_cast<float*>(buf);
@@ -513,7 +521,7 @@ pass_x(const __grid_constant__ PassParams p)
         const int xx = (hi * 4 + lo) * 4;
         const int line = line0 + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + (size_t)line * N + xx));
+        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + off + (size_t)line * N + xx));
         bf[((xx + 0) * CPAD) * 2 + r] = v.x;
         bf[((xx + 1) * CPAD) * 2 + r] = v.y;
         bf[((xx + 2) * CPAD) * 2 + r] = v.z;
@@ -549,7 +557,7 @@ pass_x(const __grid_constant__ PassParams p)
         float d[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) d[e] = bf[((xx + e) * CPAD) * 2 + r];
-        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d);
+        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d, off, soff);
     }
 }
 

@@ -57,6 +57,7 @@ def _load():
                 "es_source_add": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_add_force": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_clear": ([vp], c_int),
+                "es_batch_set": ([vp, c_int, vp, vp, vp, c_int], c_int),
                 "es_state_reset": ([vp], c_int),
                 "es_state_get": ([vp, vp], c_int),
                 "es_state_set": ([vp, vp], c_int),
@@ -65,6 +66,8 @@ def _load():
                 "es_superpose_noalloc": ([vp, c_int, c_int, c_int, vp, vp, vp, c_int, c_double, c_int, vp, vp],
                                          c_int),
                 "es_seabed_receivers": ([vp, c_int, c_int, pi], c_int),
+                "es_run_group": ([c_int, ctypes.POINTER(vp), c_int, ctypes.POINTER(c_double), ctypes.POINTER(vp),
+                                  pi, ctypes.POINTER(vp)], c_int),
                 "es_derivative": ([vp, c_int, c_int, c_int, c_int, c_double, c_int, vp, vp], c_int),
                 "es_last_step_kernel_ms": ([vp, ctypes.POINTER(ctypes.c_float), c_int], c_int),
                 "es_kernels_per_step": ([vp], c_int),
@@ -84,8 +87,8 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream",
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_force",
-            "es_source_clear", "es_state_reset", "es_state_get", "es_state_set", "es_run",
-            "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
+            "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
+            "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
             "es_kernels_per_step", "es_model_destroy", "es_status_string", "es_last_error"]
 
 
@@ -165,6 +168,30 @@ def es_superpose_noalloc(traces, src_of_event, amps, t0s, dt, n_out, gather, str
     return gather
 
 
+def es_run_group(models, nt, dts, receivers, traces=None):
+    """Advance several models together in one graph (es_run_group); returns
+    the list of trace arrays (shape as Model.run)."""
+    lib = _load()
+    n = len(models)
+    hs = (ctypes.c_void_p * n)(*[m._h for m in models])
+    dd = (ctypes.c_double * n)(*[float(v) for v in dts])
+    keep, rp, nr, tp = [], (ctypes.c_void_p * n)(), (ctypes.c_int * n)(), (ctypes.c_void_p * n)()
+    out = []
+    for i, (m, rc) in enumerate(zip(models, receivers)):
+        p_, k_ = _ptr(rc, np.int32)
+        keep.append(k_)
+        rp[i] = p_
+        nr[i] = int(np.prod(rc.shape)) // 3
+        tr = traces[i] if traces is not None else np.empty(
+            (4, nr[i], int(nt)) if m.nsim == 1 else (m.nsim, 4, nr[i], int(nt)), np.float32)
+        t_, tk = _ptr(tr, np.float32)
+        keep.append(tk)
+        tp[i] = t_
+        out.append(tr)
+    _check(lib.es_run_group(n, hs, int(nt), dd, rp, nr, tp), "es_run_group")
+    return out
+
+
 def es_derivative(f, axis, d, shift, out, stream=None):
     """out = D_axis^(shift) f for [nz][ny][nx] torch CUDA tensors."""
     lib = _load()
@@ -186,6 +213,7 @@ class Model:
 
     def __init__(self, rho, cp, cs, dx=10.0, pml=10, dy=None, dz=None, stream=None):
         self.shape = tuple(rho.shape)
+        self.nsim = 1
         self._lib = _load()
         self._h = es_model_create(rho, cp, cs, dx, pml)
         self.pml = int(pml)
@@ -241,6 +269,18 @@ class Model:
     def source_add_force(self, pos, f, wavelet):
         self._src(self._lib.es_source_add_force, pos, f, 3, wavelet)
 
+    def batch_set(self, pos, mt, wavelets):
+        """nb simulations sharing this model, one moment source each:
+        pos [nb][3] int, mt [nb][6] (xx yy zz xy xz yz), wavelets [nb][nw]."""
+        pos = np.ascontiguousarray(pos, np.int32).reshape(-1, 3)
+        nb = pos.shape[0]
+        mt = np.ascontiguousarray(mt, np.float64).reshape(nb, 6)
+        wp, wk = _ptr(wavelets, np.float32)
+        nw = int(wavelets.shape[-1])
+        _check(self._lib.es_batch_set(self._h, nb, ctypes.c_void_p(pos.ctypes.data), ctypes.c_void_p(mt.ctypes.data),
+                                      wp, nw), "es_batch_set")
+        self.nsim = nb
+
     def source_clear(self):
         _check(self._lib.es_source_clear(self._h), "es_source_clear")
 
@@ -250,7 +290,7 @@ class Model:
     def state_get(self, out=None):
         nz, ny, nx = self.shape
         if out is None:
-            out = np.empty((9, nz, ny, nx), np.float32)
+            out = np.empty((9, nz, ny, nx) if self.nsim == 1 else (self.nsim, 9, nz, ny, nx), np.float32)
         op, ok = _ptr(out, np.float32)
         _check(self._lib.es_state_get(self._h, op), "es_state_get")
         return out
@@ -269,7 +309,8 @@ class Model:
             rp, rk = _ptr(receivers, np.int32)
             n_rcv = int(np.prod(receivers.shape)) // 3
         if traces is None:
-            traces = np.empty((4, n_rcv, int(nt)), np.float32)
+            shape = (4, n_rcv, int(nt)) if self.nsim == 1 else (self.nsim, 4, n_rcv, int(nt))
+            traces = np.empty(shape, np.float32)
         tp, tk = _ptr(traces, np.float32)
         _check(self._lib.es_run(self._h, int(nt), float(dt), rp, n_rcv, tp if n_rcv else None), "es_run")
         return traces
