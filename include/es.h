@@ -189,6 +189,24 @@ int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv);
 int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out,
                   void* stream);
 
+/* FFT plan autotuner: for each axis length of this model with more than one
+ * two-stage plan (radix order R1 x R2), times the model's own velocity and
+ * stress passes (reps launches after one warm-up, CUDA events on the model's
+ * stream) with every candidate, keeps the fastest per pass kind (x pass, y/z
+ * passes) and length for the rest of the process, and records the choice
+ * in the plan cache ($ES_TUNE_CACHE, else $HOME/.cache/es_fft_plans.txt,
+ * keyed by device name), which every process loads when it creates its first
+ * model.  Resets the model's state.  report (optional): the timings, one line
+ * per candidate. */
+int es_model_autotune(es_model* m, int reps, char* report, int report_len);
+
+/* The plan in use for pass kind 0 (x) or 1 (y/z) and axis length n. */
+int es_fft_plan(int pass_kind, int n, int* ra, int* rb);
+
+/* Pins the plan ra x rb (one of the candidates for n) for pass kind 0 (x) or
+ * 1 (y/z) in this process.  ES_ERR_SIZE if it is not a candidate. */
+int es_fft_plan_select(int pass_kind, int n, int ra, int rb);
+
 /* Device time [ms] of each kernel of the last time step of the last es_run
  * (CUDA events around each kernel launch of that step), in launch order:
  * vel-x, vel-y, vel-z, str-x, str-y, str-z, inject, record.  n = capacity;

@@ -13,9 +13,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
+#include <string>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include "../../include/es.h"
 #include "es_internal.h"
@@ -65,12 +71,71 @@ int fetch(const T* src, size_t n, std::vector<T>& out, cudaStream_t st)
 
 int g_prepared_dev = -1;
 
+// On-disk cache of autotuned FFT plans: lines "device|kind|n|ra|rb" in
+// $ES_TUNE_CACHE, else $HOME/.cache/es_fft_plans.txt.
+std::string plan_cache_path()
+{
+    if (const char* p = std::getenv("ES_TUNE_CACHE")) return p;
+    if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/es_fft_plans.txt";
+    return "";
+}
+
+std::string device_name()
+{
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string n = prop.name;
+    for (char& c : n)
+        if (c == '|' || c == '\n') c = ' ';
+    return n;
+}
+
+void load_plan_cache()
+{
+    const std::string path = plan_cache_path();
+    if (path.empty()) return;
+    std::ifstream in(path);
+    const std::string dev = device_name();
+    std::string line;
+    while (std::getline(in, line)) {
+        std::stringstream ss(line);
+        std::string d, f;
+        int v[4], k = 0;
+        if (!std::getline(ss, d, '|') || d != dev) continue;
+        while (k < 4 && std::getline(ss, f, '|')) v[k++] = std::atoi(f.c_str());
+        if (k == 4) plan_select(v[0], v[1], v[2], v[3]);
+    }
+}
+
+void store_plan_cache(const std::vector<std::string>& keys, const std::vector<std::string>& lines)
+{
+    const std::string path = plan_cache_path();
+    if (path.empty()) return;
+    std::vector<std::string> keep;
+    {
+        std::ifstream in(path);
+        std::string line;
+        while (std::getline(in, line)) {
+            bool replaced = false;
+            for (const auto& k : keys) replaced |= line.rfind(k, 0) == 0;
+            if (!replaced && !line.empty()) keep.push_back(line);
+        }
+    }
+    for (const auto& l : lines) keep.push_back(l);
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // one missing level
+    std::ofstream out(path, std::ios::trunc);
+    for (const auto& l : keep) out << l << "\n";
+}
+
 int ensure_prepared()
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (g_prepared_dev != dev) {
         CK(prepare_pass_kernels());
+        load_plan_cache();
         g_prepared_dev = dev;
     }
     return ES_OK;
@@ -915,6 +980,91 @@ int es_run_group(int nmod, es_model* const* models, int nt, const double* dts, c
         if (r != ES_OK && worst == ES_OK) worst = r;
     }
     return worst;
+}
+
+int es_model_autotune(es_model* m, int reps, char* report, int report_len)
+{
+    if (!m || reps < 1) return ES_ERR_ARG;
+    double dt = 0.0;
+    int rc = run_prepare(m, 1, &dt, nullptr, 0, nullptr);
+    if (rc != ES_OK) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::string rep;
+    std::vector<std::string> keys, lines;
+    const std::string dev = device_name();
+    for (int kind = 0; kind < 2 && rc == ES_OK; ++kind) {
+        std::vector<int> lens;
+        if (kind == 0) lens.push_back(m->nx);
+        else {
+            lens.push_back(m->ny);
+            if (m->nz != m->ny) lens.push_back(m->nz);
+        }
+        for (int n : lens) {
+            int ra[8], rb[8];
+            const int nc = plan_candidates(n, ra, rb, 8);
+            if (nc < 2) continue;
+            float best = 1e30f;
+            int bi = 0;
+            for (int c = 0; c < nc && rc == ES_OK; ++c) {
+                plan_select(kind, n, ra[c], rb[c]);
+                float total = 0.f;
+                for (int a = 0; a < 3; ++a) {
+                    if ((kind == 0) != (a == 0) || axis_len(m, a) != n) continue;
+                    for (int half = 0; half < 2; ++half) {
+                        const PassParams p = make_pass(m, a, half == 1, (float)dt);
+                        cudaError_t e = launch_pass(p, m->stream);  // warm-up
+                        if (e == cudaSuccess) e = cudaEventRecord(e0, m->stream);
+                        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_pass(p, m->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, m->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                        if (e != cudaSuccess) {
+                            rc = cuda_fail(e, "es_model_autotune");
+                            break;
+                        }
+                        total += ms / reps;
+                    }
+                }
+                char buf[96];
+                snprintf(buf, sizeof buf, "%s n=%d %dx%d %.4f ms\n", kind == 0 ? "x" : "yz", n, ra[c], rb[c], total);
+                rep += buf;
+                if (total < best) {
+                    best = total;
+                    bi = c;
+                }
+            }
+            plan_select(kind, n, ra[bi], rb[bi]);
+            char key[160], line[200];
+            snprintf(key, sizeof key, "%s|%d|%d|", dev.c_str(), kind, n);
+            snprintf(line, sizeof line, "%s%d|%d", key, ra[bi], rb[bi]);
+            keys.push_back(key);
+            lines.push_back(line);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ES_OK) return rc;
+    store_plan_cache(keys, lines);
+    if (report && report_len > 0) {
+        std::strncpy(report, rep.c_str(), (size_t)report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return es_state_reset(m);
+}
+
+int es_fft_plan_select(int pass_kind, int n, int ra, int rb)
+{
+    if (pass_kind < 0 || pass_kind > 1) return ES_ERR_ARG;
+    return plan_select(pass_kind, n, ra, rb) ? ES_OK : ES_ERR_SIZE;
+}
+
+int es_fft_plan(int pass_kind, int n, int* ra, int* rb)
+{
+    if (!ra || !rb || pass_kind < 0 || pass_kind > 1) return ES_ERR_ARG;
+    return plan_current(pass_kind, n, ra, rb) ? ES_OK : ES_ERR_SIZE;
 }
 
 int es_last_step_kernel_ms(es_model* m, float* ms, int n)

@@ -50,6 +50,11 @@ struct PassParams {
 
 // Plan of the two-stage FFT for an axis length (0 if unsupported).
 int plan_radices(int n, int* ra, int* rb);
+// Candidate plans for n (up to cap), and the plan in use per pass kind
+// (0 = x pass, 1 = y/z passes): read and select.
+int plan_candidates(int n, int* ra, int* rb, int cap);
+int plan_current(int kind, int n, int* ra, int* rb);
+int plan_select(int kind, int n, int ra, int rb);
 // Launches one pass (all jobs) along p.axis.  Returns a cudaError_t.
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
 // Opts every pass kernel into the shared memory it needs (once per device).

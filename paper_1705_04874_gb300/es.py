@@ -71,6 +71,9 @@ def _load():
                 "es_derivative": ([vp, c_int, c_int, c_int, c_int, c_double, c_int, vp, vp], c_int),
                 "es_last_step_kernel_ms": ([vp, ctypes.POINTER(ctypes.c_float), c_int], c_int),
                 "es_kernels_per_step": ([vp], c_int),
+                "es_model_autotune": ([vp, c_int, ctypes.c_char_p, c_int], c_int),
+                "es_fft_plan": ([c_int, c_int, pi, pi], c_int),
+                "es_fft_plan_select": ([c_int, c_int, c_int, c_int], c_int),
                 "es_model_destroy": ([vp], None),
                 "es_status_string": ([c_int], ctypes.c_char_p),
                 "es_last_error": ([], ctypes.c_char_p),
@@ -89,7 +92,8 @@ def exported_symbols():
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_force",
             "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
             "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
-            "es_kernels_per_step", "es_model_destroy", "es_status_string", "es_last_error"]
+            "es_kernels_per_step", "es_model_autotune", "es_fft_plan",
+            "es_fft_plan_select", "es_model_destroy", "es_status_string", "es_last_error"]
 
 
 def _check(status, where):
@@ -190,6 +194,22 @@ def es_run_group(models, nt, dts, receivers, traces=None):
         out.append(tr)
     _check(lib.es_run_group(n, hs, int(nt), dd, rp, nr, tp), "es_run_group")
     return out
+
+
+def es_fft_plan(pass_kind, n):
+    """(RA, RB) of the plan in use for pass kind 0 (x) / 1 (y, z) and length n."""
+    ra, rb = ctypes.c_int(), ctypes.c_int()
+    _check(_load().es_fft_plan(int(pass_kind), int(n), ctypes.byref(ra), ctypes.byref(rb)), "es_fft_plan")
+    return ra.value, rb.value
+
+
+def es_fft_plan_select(pass_kind, n, ra, rb):
+    _check(_load().es_fft_plan_select(int(pass_kind), int(n), int(ra), int(rb)), "es_fft_plan_select")
+
+
+PLAN_CANDIDATES = {16: [(4, 4)], 32: [(8, 4), (4, 8)], 48: [(12, 4), (4, 12)], 64: [(16, 4), (8, 8), (4, 16)],
+                   80: [(16, 5), (5, 16)], 96: [(16, 6), (6, 16)], 128: [(16, 8), (8, 16)],
+                   160: [(16, 10), (10, 16)], 192: [(16, 12), (12, 16)], 256: [(16, 16)]}
 
 
 def es_derivative(f, axis, d, shift, out, stream=None):
@@ -327,6 +347,13 @@ class Model:
         if n < 0:
             raise EsError(n, "es_last_step_kernel_ms")
         return [buf[i] for i in range(n)]
+
+    def autotune(self, reps=5):
+        """Time every FFT plan candidate on this model's passes and keep the
+        fastest (es_model_autotune); returns the timing report."""
+        buf = ctypes.create_string_buffer(4096)
+        _check(self._lib.es_model_autotune(self._h, int(reps), buf, 4096), "es_model_autotune")
+        return buf.value.decode()
 
     def kernels_per_step(self):
         return int(self._lib.es_kernels_per_step(self._h))
