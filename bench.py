@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1705_04874_gb300 import synth  # noqa: E402
+from paper_1705_04874_gb300.replicas import max_over_ranks, sum_over_ranks  # noqa: E402
 
 # algorithmic bytes per cell for one launch of each pass kernel (FP32):
 # velocity pass: 3 jobs x (read source + read/write target + read buoyancy)
@@ -143,24 +144,6 @@ def dist_setup(gpus):
 def barrier(dist):
     if dist is not None:
         dist.barrier()
-
-
-def max_over_ranks(dist, v):
-    if dist is None:
-        return v
-    import torch
-    t = torch.tensor([v], dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def sum_over_ranks(dist, v):
-    if dist is None:
-        return v
-    import torch
-    t = torch.tensor([v], dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
 
 
 def oracle_sample(w, inp, steps, nthreads=0):
