@@ -1,0 +1,129 @@
+"""The learned surrogate on the GPU: its BF16/FP32 GEMM in every storage
+order, its loss and gradients against the FP64 oracle (oracle/surrogate.py),
+and the whole workflow on a small model -- solver catalog, training on the
+GPU, error gate, serving with the solver as fallback -- where every served
+seismogram is checked against the exact solver reference."""
+import numpy as np
+import pytest
+
+from paper_1705_04874_gb300 import synth
+from conftest import cfl_dt
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_04874_gb300 import es, surrogate
+    es._load()
+    return es, surrogate, torch
+
+
+def _bf(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda().to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("a_t", [False, True])
+@pytest.mark.parametrize("b_nk", [False, True])
+@pytest.mark.parametrize("split", [1, 3])
+def test_gemm_all_layouts(env, a_t, b_nk, split):
+    es, sur, torch = env
+    rng = np.random.default_rng(int(a_t) * 4 + int(b_nk) * 2 + split)
+    M, N, K = 200, 136, 328  # ragged against the 128 x 128 x 32 tiles
+    A = rng.standard_normal((K, M) if a_t else (M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K) if b_nk else (K, N)).astype(np.float32)
+    Ab, Bb = _bf(torch, A), _bf(torch, B)
+    A64 = Ab.float().cpu().numpy().astype(np.float64)  # the BF16-rounded operands
+    B64 = Bb.float().cpu().numpy().astype(np.float64)
+    opA = A64.T if a_t else A64
+    opB = B64.T if b_nk else B64
+    C0 = rng.standard_normal((M, N)).astype(np.float32)
+    C = torch.from_numpy(C0.copy()).cuda()
+    sur.es_gemm_bf16(Ab, Bb, C, a_t=a_t, b_nk=b_nk, alpha=0.5, beta=-2.0, split_k=split)
+    ref = 0.5 * opA @ opB - 2.0 * C0
+    got = C.cpu().numpy()
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_loss_and_gradients_match_oracle(env):
+    es, sur, torch = env
+    from oracle import surrogate as osur
+    cfg = dict(nfreq=2, hidden=64, latent=16, n_rcv=4, nt=16)
+    s = sur.Surrogate(cfg["n_rcv"], cfg["nt"], nfreq=2, hidden=64, latent=16, max_batch=16, seed=3)
+    try:
+        rng = np.random.default_rng(5)
+        lay, P, F, D = osur.layout(**cfg)
+        assert s.num_params() == P
+        params = (rng.standard_normal(P) * 0.2).astype(np.float32)
+        s.set_params(params)
+        scale = [1.5, 0.7, 0.9, 1.1]
+        s.set_output_scale(scale)
+        B = 16
+        pos = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+        mt = rng.standard_normal((B, 6)).astype(np.float32)
+        tgt = rng.standard_normal((B, D)).astype(np.float32)
+        cu = lambda a: torch.from_numpy(a).cuda()
+        loss, per, g = s.loss_grad(cu(pos), cu(mt), cu(tgt))
+        # the oracle sees the parameters the GPU multiplies with (BF16-rounded weights)
+        pb = torch.from_numpy(params).to(torch.bfloat16).float().numpy().astype(np.float64)
+        pr = params.astype(np.float64).copy()
+        for name in ("W1", "W2", "W3", "Wd"):
+            o, shp = lay[name]
+            pr[o:o + int(np.prod(shp))] = pb[o:o + int(np.prod(shp))]
+        oloss, oper, og = osur.loss_and_grads(pr, cfg, pos, mt, tgt, scale)
+        assert abs(loss - oloss) <= 2e-2 * oloss
+        assert np.allclose(per.cpu().numpy(), oper, rtol=3e-2)
+        g = g.cpu().numpy().astype(np.float64)
+        # BF16 operands round to 2^-9 relative; the gradient of the first layer
+        # sits behind five such roundings (dU, dA, dH2, dH1, x), the others behind fewer
+        tol = {"W1": 6e-2, "b1": 6e-2}
+        for name, (o, shp) in lay.items():
+            n = int(np.prod(shp))
+            a, b = g[o:o + n], og[o:o + n]
+            assert np.linalg.norm(a - b) <= tol.get(name, 3e-2) * np.linalg.norm(b), name
+        y = s.predict(cu(pos), cu(mt)).cpu().numpy()
+        assert np.linalg.norm(y - osur.forward(pr, cfg, pos, mt, scale)["Y"]) <= 1e-2 * np.linalg.norm(y)
+    finally:
+        s.close()
+
+
+def test_catalog_train_gate_serve(env):
+    """Small marine model, 24 catalog locations: the surrogate learns their
+    Green's functions from 144 solver runs (unit moment tensors), is trained
+    on fresh random moment tensors every epoch, the gate keeps the locations it
+    reproduces within 5 %, and every served seismogram (surrogate or solver)
+    is within 5 % of the exact reference."""
+    es, sur, torch = env
+    shape = (48, 32, 32)
+    rho, cp, cs = synth.marine_model(shape=shape, seed=4)
+    pml, nt = 4, 256  # long enough for the full arrivals at every receiver
+    dt = cfl_dt(cp, 10.0)
+    wav = synth.ricker(nt, dt, 30.0)
+    box = synth.reservoir_box(shape, pml)
+    rng = synth.SplitMix64(6)
+    locations = synth.latin_hypercube_positions(rng, box, 24)
+    with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
+        rcv = m.seabed_receivers(2, 2)
+        G = sur.green_catalog(m, locations, nt, dt, rcv, wav, per_batch=8)
+        pos_n = sur.normalize_positions(locations, box)
+        s = sur.Surrogate(len(rcv), nt, nfreq=3, hidden=128, latent=64, max_batch=48, seed=1)
+        try:
+            hist = sur.train(s, pos_n, G, epochs=200, lr=3e-3)
+            assert hist[-1] < 1e-4 * hist[0]
+            trusted, errs = sur.calibrate_gate(s, pos_n, G, n_val=3)
+            assert trusted.mean() >= 0.75, errs.max(axis=1)
+            # serve random sources at catalog locations
+            loc = np.floor(synth.SplitMix64(9).uniform(40) * len(locations)).astype(int)
+            mts = np.array([synth.random_dc(rng) for _ in loc])
+            out, used_solver = sur.serve(s, pos_n, trusted, loc, mts, m, locations, nt, dt, rcv, wav)
+            ref = sur.combine(G, loc, mts)
+            # whole-seismogram relative L2 with each component divided by its RMS over the catalog
+            sc = G.permute(2, 0, 1, 3, 4).reshape(4, -1).pow(2).mean(dim=1).sqrt().view(1, 4, 1, 1)
+            d = ((out - ref) / sc).reshape(len(loc), -1).norm(dim=1) / (ref / sc).reshape(len(loc), -1).norm(dim=1)
+            assert float(d.max()) < 0.05, float(d.max())
+            assert used_solver.sum() == (~trusted[loc]).sum()
+        finally:
+            s.close()
