@@ -194,13 +194,21 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="256", choices=["256", "128"])
+    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate"])
+    ap.add_argument("--sur-locations", type=int, default=682)
+    ap.add_argument("--sur-epochs", type=int, default=150)
+    ap.add_argument("--sur-hidden", type=int, default=768)
+    ap.add_argument("--sur-latent", type=int, default=768)
+    ap.add_argument("--sur-nfreq", type=int, default=9)
+    ap.add_argument("--sur-lr", type=float, default=3e-3)
     ap.add_argument("--nt", type=int, default=0, help="override time steps per es_run (diagnostics)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-nt", type=int, default=200, help="time steps of the batched measurement")
     args = ap.parse_args()
+    if args.workload == "surrogate":
+        return measure_surrogate(args)
     w = workload(args.workload)
     if args.nt:
         w["nt"] = args.nt
@@ -388,6 +396,134 @@ def measure_batched(es, nt, reps, stream):
     return {"value": round(value, 1), "unit": "Mcell-steps/s", "plain_value": round(plain, 1), "plans": plans,
             "speedup_vs_plain": round(value / plain, 3), "time_steps": nt, "ms_per_run": round(ms, 2),
             "workload": "64 sources on 128^3 + 16 on 96^3 + 8 on 160^3 marine models, one graph, 32x32 receivers"}
+
+
+def measure_surrogate(args):
+    """Surrogate workload: 96^3 marine model, PML 10, 8 x 8 seabed receivers,
+    1024 samples, Ricker 30 Hz; a catalog of 682 Latin-hypercube locations
+    in the reservoir box whose 6 unit-moment responses come from 4092 solver
+    runs; training on the GPU; 10,000 random sources (catalog location,
+    random double couple) served by the surrogate where the gate trusts the
+    location and by the solver elsewhere.  Metric: seismograms/s."""
+    import torch
+    from paper_1705_04874_gb300 import es, surrogate as sur
+    torch.cuda.set_device(0)
+    n, pml, nt, f0 = 96, 10, 1024, 30.0
+    rho, cp, cs = synth.marine_model(n, seed=1)
+    dt = 0.3 * 10.0 / float(cp.max())
+    wav = synth.ricker(nt, dt, f0)
+    box = synth.reservoir_box((n, n, n), pml)
+    n_loc = args.sur_locations
+    locations = synth.latin_hypercube_positions(synth.SplitMix64(4), box, n_loc)
+    m = es.Model(rho, cp, cs, dx=10.0, pml=pml)
+    rcv = m.seabed_receivers(8, 8)
+    out = {"workload": f"96^3 marine, 64 receivers x 1024 samples, {n_loc} catalog locations x 6 unit moment "
+                       f"tensors ({6 * n_loc} solver runs), 10000 served sources"}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = sur.green_catalog(m, locations, nt, dt, rcv, wav, per_batch=16)
+    torch.cuda.synchronize()
+    t_cat = time.perf_counter() - t0
+    out["catalog_s"] = round(t_cat, 2)
+    solver_rate = 6 * n_loc / t_cat  # seismogram sets per second, batched solver
+    pos_n = sur.normalize_positions(locations, box)
+    s = sur.Surrogate(len(rcv), nt, nfreq=args.sur_nfreq, hidden=args.sur_hidden, latent=args.sur_latent,
+                      max_batch=256, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = sur.train(s, pos_n, G, epochs=args.sur_epochs, lr=args.sur_lr)
+    torch.cuda.synchronize()
+    out["train_s"] = round(time.perf_counter() - t0, 2)
+    out["train_loss"] = [float(f"{hist[0]:.3e}"), float(f"{hist[-1]:.3e}")]
+    trusted, errs = sur.calibrate_gate(s, pos_n, G, n_val=4)
+    out["trusted_locations"] = round(float(trusted.mean()), 4)
+    e_loc = errs.max(axis=1)
+    out["gate_err_median"] = float(f"{np.median(e_loc):.3e}")
+    out["gate_err_max"] = float(f"{e_loc.max():.3e}")
+    rng = synth.SplitMix64(11)
+    n_src = 10000
+    loc = np.minimum(np.floor(rng.uniform(n_src) * n_loc).astype(int), n_loc - 1)
+    mts = np.array([synth.random_dc(rng) for _ in range(n_src)])
+    # surrogate alone on all sources (rate of the network)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = torch.empty((256, 4 * len(rcv) * nt), device="cuda")
+    for b in range(0, n_src, 256):
+        idx = np.arange(b, min(n_src, b + 256))
+        k = (len(idx) + 7) // 8 * 8
+        idx = np.concatenate([idx, np.repeat(idx[:1], k - len(idx))])
+        s.predict(torch.from_numpy(pos_n[loc[idx]]).cuda(), torch.from_numpy(mts[idx].astype(np.float32)).cuda(),
+                  res[:k])
+    torch.cuda.synchronize()
+    sur_rate = n_src / (time.perf_counter() - t0)
+    # served pipeline (surrogate where trusted, solver elsewhere) on all the sources, or on
+    # the first 1000 when the gate sends more than 2 % of the locations to the solver
+    n_pipe = n_src if trusted.mean() >= 0.98 else 1000
+    del res
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    served, used_solver = sur.serve(s, pos_n, trusted, loc[:n_pipe], mts[:n_pipe], m, locations, nt, dt, rcv, wav,
+                                    batch_solver=32)
+    torch.cuda.synchronize()
+    pipe_rate = n_pipe / (time.perf_counter() - t0)
+    # every served seismogram against the exact solver reference (linear combination of
+    # the solver's unit responses), in chunks
+    sc = G.permute(2, 0, 1, 3, 4).reshape(4, -1).pow(2).mean(dim=1).sqrt().view(1, 4, 1, 1)
+    d = torch.empty(n_pipe, device="cuda")
+    for b in range(0, n_pipe, 500):
+        e = min(n_pipe, b + 500)
+        ref = sur.combine(G, loc[b:e], mts[b:e])
+        d[b:e] = ((served[b:e] - ref) / sc).reshape(e - b, -1).norm(dim=1) / (ref / sc).reshape(e - b, -1).norm(dim=1)
+        del ref
+    out["pipeline_sources"] = n_pipe
+    # throughput of the network's GEMMs: tcgen05 (both operands K-major: inference decoder,
+    # dZ), mma.sync (the other storage orders), and the decoder product at the served shape
+    def gemm_tflops(M, N, K, b_nk, reps=5):
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda").to(torch.bfloat16) if b_nk else \
+            torch.randn(K, N, device="cuda").to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
+        e1.record()
+        torch.cuda.synchronize()
+        sur.es_gemm_status()
+        return 2.0 * M * N * K * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    K6 = 6 * args.sur_latent
+    gemm = {"tcgen05_8192": round(gemm_tflops(8192, 8192, 8192, True), 1),
+            "mma_sync_8192": round(gemm_tflops(8192, 8192, 8192, False), 1),
+            f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(256, s.D, K6, True), 1)}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    dec = gemm[f"tcgen05_decoder_256x{s.D}x{K6}"]
+    out.update({"solver_seismograms_per_s": round(solver_rate, 2), "surrogate_seismograms_per_s": round(sur_rate, 1),
+                "pipeline_seismograms_per_s": round(pipe_rate, 1),
+                "pipeline_solver_fraction": round(float(used_solver.mean()), 4),
+                "served_max_rel_l2": float(f"{float(d.max()):.3e}"),
+                "speedup_surrogate_vs_solver": round(sur_rate / solver_rate, 1),
+                "speedup_pipeline_vs_solver": round(pipe_rate / solver_rate, 1),
+                "gemm_tflops": gemm,
+                "served_over_5pct": int((d > 0.05).sum()),
+                "network": {"hidden": args.sur_hidden, "latent": args.sur_latent, "nfreq": args.sur_nfreq,
+                            "params": s.num_params(), "epochs": args.sur_epochs, "lr": args.sur_lr}})
+    s.close()
+    m.close()
+    print(json.dumps({"metric": "seismograms/s", "value": out["pipeline_seismograms_per_s"],
+                      "unit": "4C seismogram sets/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16/f32",
+                      "data": "synthetic", "config": {"workload": out["workload"]},
+                      "roofline": {"bound": "tensor", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
+                                   "achieved": dec, "peak": peak, "unit": "TFLOP/s", "frac": round(dec / peak, 4),
+                                   "traffic": None, "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"},
+                      "surrogate": out}))
+    return 0
 
 
 def e2e(es, w, inp, stream):

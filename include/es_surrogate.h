@@ -85,10 +85,19 @@ int es_sur_combine(const float* G, int n_loc, long long D, const int* loc, const
  * FP32 C, all device memory.  A is row-major [M][K] (lda), or stored [K][M]
  * when a_t; B is stored [N][K] when b_nk, else [K][N].  K, lda, ldb multiples
  * of 8 (and M when a_t, N when !b_nk).  split_k > 1 splits K across CTAs
- * (atomic FP32 adds: summation order not fixed).  Tensor-core mma.sync
- * m16n8k16 bf16 with FP32 accumulation. */
+ * (atomic FP32 adds: summation order not fixed).  FP32 accumulation.
+ * Both operands K-major (a_t == 0, b_nk != 0; A and B 16-byte aligned): the
+ * fifth-generation tensor cores -- TMA-fed 4-stage shared-memory ring,
+ * tcgen05.mma 128 x 256 x 16 into a tensor-memory accumulator, 128 x 256
+ * tiles.  Other storage orders: mma.sync m16n8k16 with ldmatrix operands.
+ * Device waits in the tcgen05 kernel are bounded; see es_gemm_status. */
 int es_gemm_bf16(int M, int N, int K, const void* A, int lda, int a_t, const void* B, int ldb, int b_nk, float* C,
                  int ldc, float alpha, float beta, int split_k, void* stream);
+
+/* Synchronizes the device, then reports and clears the tcgen05 GEMM's
+ * device status word: ES_OK, or ES_ERR_TIMEOUT if any of its bounded
+ * mbarrier waits ran out since the last call (that launch's C is undefined). */
+int es_gemm_status(void);
 
 #ifdef __cplusplus
 }

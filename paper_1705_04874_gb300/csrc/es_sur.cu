@@ -28,6 +28,10 @@ struct es_sur {
     __nv_bfloat16 *X, *H1b, *H2b, *Zb, *dUb, *dAb, *dH2b, *dH1b;
     float *H1, *H2, *A, *U, *dZ, *dA, *dH2, *dH1, *loss, *acc;
     int t = 0;
+    // inference copy of the decoder, K-major for the tcgen05 GEMM: WdT [D][6K],
+    // rebuilt from the BF16 mirror whenever the parameters changed (ver)
+    __nv_bfloat16* WdT = nullptr;
+    long long ver = 0, wdt_ver = -1;
 };
 
 namespace {
@@ -54,8 +58,9 @@ int check_batch(const es_sur* s, const void* pos, const void* mt, int B)
     return ES_OK;
 }
 
-// forward through the decoder: s->U = z Wd (normalized units)
-int forward(es_sur* s, const float* pos, const float* mt, int B)
+// forward through the decoder: s->U = z Wd (normalized units); for inference
+// the decoder product runs K-major on the tcgen05 tensor cores (z WdT^T)
+int forward(es_sur* s, const float* pos, const float* mt, int B, bool infer = false)
 {
     const __nv_bfloat16* W1 = s->pb + s->oW1;
     const __nv_bfloat16* W2 = s->pb + s->oW2;
@@ -69,8 +74,12 @@ int forward(es_sur* s, const float* pos, const float* mt, int B)
     CKS(gemm_bf16(B, s->K, s->H, s->H2b, s->H, false, W3, s->K, false, s->A, s->K, 1.f, 0.f, 1, s->st));
     CKS(sur_bias_act(s->A, s->p + s->ob3, B, s->K, false, nullptr, s->st));
     CKS(sur_outer(mt, s->A, B, s->K, s->Zb, s->st));
-    CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, Wd, (int)s->D, false, s->U, (int)s->D, 1.f, 0.f, 1,
-                  s->st));
+    if (infer)
+        CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT, 6 * s->K, true, s->U, (int)s->D, 1.f,
+                      0.f, 1, s->st));
+    else
+        CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, Wd, (int)s->D, false, s->U, (int)s->D, 1.f, 0.f,
+                      1, s->st));
     return ES_OK;
 }
 
@@ -190,6 +199,7 @@ int es_sur_create(const es_sur_config* cfg, es_sur** out)
 void es_sur_destroy(es_sur* s)
 {
     if (!s) return;
+    cudaFree(s->WdT);
     cudaFree(s->pool);
     delete s;
 }
@@ -217,6 +227,7 @@ int es_sur_set_params(es_sur* s, const float* params)
     CKS(cudaMemcpyAsync(s->p, params, sizeof(float) * s->P, cudaMemcpyDefault, s->st));
     CKS(cast_bf16(s->p, s->pb, s->P, s->st));
     CKS(cudaStreamSynchronize(s->st));
+    s->ver += 1;
     return ES_OK;
 }
 
@@ -249,7 +260,16 @@ int es_sur_predict(es_sur* s, const float* pos, const float* mt, int B, float* o
     if (rc != ES_OK) return rc;
     if (!out || !dev_ptr(out)) return ES_ERR_ARG;
     cudaGetLastError();
-    if ((rc = forward(s, pos, mt, B)) != ES_OK) return rc;
+    if (!s->WdT && cudaMalloc(&s->WdT, sizeof(__nv_bfloat16) * 6 * s->K * s->D) != cudaSuccess) {
+        cudaGetLastError();
+        s->WdT = nullptr;
+        return ES_ERR_OOM;
+    }
+    if (s->wdt_ver != s->ver) {
+        CKS(transpose_bf16(s->pb + s->oWd, 6LL * s->K, s->D, s->WdT, s->st));
+        s->wdt_ver = s->ver;
+    }
+    if ((rc = forward(s, pos, mt, B, true)) != ES_OK) return rc;
     CKS(sur_scale_out(s->U, s->scale, B, s->D / 4, out, s->st));
     return ES_OK;
 }
@@ -285,6 +305,7 @@ int es_sur_train_step(es_sur* s, const float* pos, const float* mt, const float*
     if ((rc = backward(s, mt, B)) != ES_OK) return rc;
     s->t += 1;
     CKS(sur_adam(s->p, s->g, s->m, s->v, s->P, lr, 0.9f, 0.999f, 1e-8f, s->t, s->pb, s->st));
+    s->ver += 1;
     if (loss) {
         CKS(cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->st));
         CKS(cudaStreamSynchronize(s->st));
@@ -301,6 +322,14 @@ int es_sur_combine(const float* G, int n_loc, long long D, const int* loc, const
     cudaGetLastError();
     CKS(sur_combine(G, D, loc, mt, B, out, static_cast<cudaStream_t>(stream)));
     return ES_OK;
+}
+
+int es_gemm_status(void)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return ES_ERR_CUDA;
+    unsigned v = 0;
+    if (gemm_tc_status(&v) != cudaSuccess) return ES_ERR_CUDA;
+    return v ? ES_ERR_TIMEOUT : ES_OK;
 }
 
 int es_gemm_bf16(int M, int N, int K, const void* A, int lda, int a_t, const void* B, int ldb, int b_nk, float* C,

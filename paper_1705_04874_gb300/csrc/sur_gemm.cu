@@ -10,6 +10,8 @@
 // through ldmatrix (transposing on the fly for the [K][M] / [K][N] storage
 // orders); global -> shared tiles move with 16-byte cp.async, double
 // buffered.  Out-of-range rows and columns are zero-filled.
+// The K-major order of both operands (A [M][K], B [N][K]) runs on the
+// tcgen05 tensor cores instead (sur_gemm_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -196,6 +198,7 @@ cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, bool
                       int ldb, bool b_nk, float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (!a_t && b_nk) return gemm_bf16_tc(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, split_k, st);
     if (split_k < 1) split_k = 1;
     int kps = (K + split_k - 1) / split_k;
     kps = (kps + BK - 1) / BK * BK;
@@ -206,8 +209,7 @@ cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, bool
         cudaError_t e = scale_f32(C, M, N, ldc, beta, st);
         if (e != cudaSuccess) return e;
     }
-    if (!a_t && b_nk) gemm_bf16_kernel<false, true><<<grid, THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kps);
-    else if (!a_t && !b_nk) gemm_bf16_kernel<false, false><<<grid, THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kps);
+    if (!a_t && !b_nk) gemm_bf16_kernel<false, false><<<grid, THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kps);
     else if (a_t && b_nk) gemm_bf16_kernel<true, true><<<grid, THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kps);
     else gemm_bf16_kernel<true, false><<<grid, THREADS, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kps);
     return cudaGetLastError();

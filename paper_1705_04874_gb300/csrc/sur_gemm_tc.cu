@@ -1,0 +1,371 @@
+// BF16-input, FP32-accumulate GEMM on the fifth-generation tensor cores
+// (tcgen05) for the K-major storage order of both operands:
+//   C[M][N] = alpha * A[M][K] * B[N][K]^T + beta * C
+// A row-major [M][K] (lda), B row-major [N][K] (ldb), C FP32 row-major (ldc).
+//
+// One CTA per 128 x 256 output tile (x split_k slices of K), 4 warps:
+//   warp 0, one thread: TMA producer -- 64-wide K slabs of A (128 rows) and
+//       B (256 rows) into a 4-stage ring of 128-byte-swizzled shared tiles,
+//       completion tracked by transaction-count mbarriers;
+//   warp 1, one thread: issues tcgen05.mma (M 128, N 256, K 16; both
+//       operands from shared-memory descriptors) into a 256-column FP32
+//       accumulator in tensor memory; tcgen05.commit frees each stage and,
+//       at the end, signals the epilogue;
+//   warps 0-3: epilogue -- warp w owns TMEM lanes (tile rows) 32w..32w+31,
+//       reads 32 columns at a time with tcgen05.ld and writes
+//       alpha * acc + beta * C (split_k > 1: atomically adds alpha * acc onto
+//       a C that already holds beta * C).
+// Rows, columns and K past the matrix edge are zero-filled by TMA and masked
+// in the epilogue.  Every mbarrier wait gives up after WAIT_NS of global
+// time, records the role that gave up in a device status word (read and
+// cleared by gemm_tc_status) and lets the CTA finish: TMA copies still in
+// flight are awaited (again bounded) and the tensor memory is always freed.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "sur_internal.h"
+
+namespace es {
+namespace {
+
+constexpr int TM = 128;  // tile rows = MMA M = TMEM lanes
+constexpr int TN = 256;  // tile columns = MMA N = TMEM columns (FP32)
+constexpr int TK = 64;   // K per stage: one 128-byte swizzle row of BF16
+constexpr int UK = 16;   // K of one tcgen05.mma kind::f16
+constexpr int STAGES = 4;
+constexpr int A_BYTES = TM * TK * 2;
+constexpr int B_BYTES = TN * TK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack for the 1024-byte swizzle atoms
+constexpr int THREADS = 128;
+constexpr unsigned TMEM_COLS = TN;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+static_assert(A_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "swizzle atoms must stay 1024-byte aligned");
+
+// instruction descriptor for kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits
+// 7-9 = 1), B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ unsigned g_tc_status;  // bit 0 producer, bit 1 MMA, bit 2 epilogue, bit 3 drain gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase of the given parity to complete
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63u) == 0 && global_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset 1024), descriptor version 1
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                   int nkb, int kb_per, int mt, int ntl, float* __restrict__ C, int ldc, float alpha, float beta,
+                   int atomic)
+{
+    extern __shared__ uint8_t dyn[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_issued, s_consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (smem_u32(dyn) + 1023u) & ~1023u;
+    int id = blockIdx.x;
+    const int mi = id % mt;
+    id /= mt;
+    const int ni = id % ntl;
+    const int kb0 = (id / ntl) * kb_per;
+    const int nk = min(nkb, kb0 + kb_per) - kb0;  // >= 1: the host sizes the slices
+    const int m0 = mi * TM, n0 = ni * TN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (kb / STAGES) & 1;
+            if (!mbar_wait(&empty[s], ph ^ 1)) {
+                atomicOr(&g_tc_status, 1u);
+                break;
+            }
+            const uint32_t sa = base + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(sa, &mapA, &full[s], (kb0 + kb) * TK, m0);
+            tma_load_2d(sa + A_BYTES, &mapB, &full[s], (kb0 + kb) * TK, n0);
+        }
+        s_issued = kb;
+    } else if (warp == 1 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (kb / STAGES) & 1;
+            if (!mbar_wait(&full[s], ph)) {
+                atomicOr(&g_tc_status, 2u);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + A_BYTES);
+#pragma unroll
+            for (int k = 0; k < TK / UK; ++k) {
+                const uint64_t step = (uint64_t)((k * UK * 2) >> 4);  // 32 bytes along the swizzled row
+                tc_mma(tmem, da + step, db + step, IDESC, (kb | k) != 0);
+            }
+            tc_commit(&empty[s]);
+        }
+        s_consumed = kb;
+        tc_commit(&done);  // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+
+    const bool got = mbar_wait(&done, 0);
+    if (!got && lane == 0) atomicOr(&g_tc_status, 4u);
+    tc_fence_after();
+    if (got) {
+        const int row = m0 + warp * 32 + lane;
+        float* crow = C + (size_t)row * ldc;
+        const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+            if (n0 + c0 >= N) break;  // uniform over the warp
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row >= M) continue;
+            const int ncol = min(32, N - n0 - c0);
+            float* p = crow + n0 + c0;
+            if (vec && ncol == 32) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
+                                           alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
+                    float4* q = reinterpret_cast<float4*>(p + j);
+                    if (atomic) {
+                        atomicAdd(q, v);
+                    } else {
+                        if (beta != 0.f) {
+                            const float4 o = *q;
+                            v.x += beta * o.x;
+                            v.y += beta * o.y;
+                            v.z += beta * o.z;
+                            v.w += beta * o.w;
+                        }
+                        *q = v;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j < ncol) {
+                        const float v = alpha * __uint_as_float(r[j]);
+                        if (atomic) atomicAdd(p + j, v);
+                        else p[j] = beta != 0.f ? v + beta * p[j] : v;
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // copies issued but never consumed (only after a wait gave up) must land before the CTA exits
+        for (int kb = s_consumed; kb < s_issued; ++kb)
+            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) {
+                atomicOr(&g_tc_status, 8u);
+                break;
+            }
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// rows x K BF16 matrix with leading dimension ld, boxes of box_rows x TK
+bool make_map(EncodeTiled fn, CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, int ld, int box_rows)
+{
+    const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dim, stride, box, estride,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
+    if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N) return cudaErrorInvalidValue;
+    EncodeTiled fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    alignas(64) CUtensorMap mapA, mapB;
+    if (!make_map(fn, &mapA, A, M, K, lda, TM) || !make_map(fn, &mapB, B, N, K, ldb, TN))
+        return cudaErrorInvalidValue;
+    const int nkb = (K + TK - 1) / TK;
+    if (split_k < 1) split_k = 1;
+    if (split_k > nkb) split_k = nkb;
+    const int kb_per = (nkb + split_k - 1) / split_k;
+    split_k = (nkb + kb_per - 1) / kb_per;  // no empty slice
+    const int mt = (M + TM - 1) / TM, ntl = (N + TN - 1) / TN;
+    const long long grid = (long long)mt * ntl * split_k;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (split_k > 1 && beta != 1.f) {
+        cudaError_t e = scale_f32(C, M, N, ldc, beta, st);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    gemm_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, nkb, kb_per, mt, ntl, C, ldc, alpha,
+                                                               beta, split_k > 1 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_tc_status(unsigned* status)
+{
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_status, sizeof v);
+    if (e != cudaSuccess) return e;
+    *status = v;
+    if (v) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof zero);
+    }
+    return e;
+}
+
+}  // namespace es

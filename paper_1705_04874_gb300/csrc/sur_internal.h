@@ -10,6 +10,15 @@ namespace es {
 cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, bool a_t, const __nv_bfloat16* B,
                       int ldb, bool b_nk, float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st);
 
+// the K-major case (A [M][K], B [N][K]) on tcgen05 tensor cores; see sur_gemm_tc.cu
+cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st);
+// reads and clears the tcgen05 GEMM's device status word (bits set by waits that gave up)
+cudaError_t gemm_tc_status(unsigned* status);
+// out[c][r] = in[r][c] for a rows x cols BF16 matrix (row-major both)
+cudaError_t transpose_bf16(const __nv_bfloat16* in, long long rows, long long cols, __nv_bfloat16* out,
+                           cudaStream_t st);
+
 cudaError_t scale_f32(float* C, int M, int N, int ldc, float s, cudaStream_t st);
 cudaError_t cast_bf16(const float* x, __nv_bfloat16* y, size_t n, cudaStream_t st);
 // position features: [p, sin(2^j pi p), cos(2^j pi p)], j < nfreq, zero padded to width

@@ -207,6 +207,37 @@ cudaError_t scale_f32(float* C, int M, int N, int ldc, float s, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// 64 x 64 tiles through shared memory (row padded by 2 elements: the column
+// reads of the second half hit 32 distinct banks)
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, long long rows, long long cols,
+                                      __nv_bfloat16* __restrict__ out)
+{
+    __shared__ __nv_bfloat16 t[64][66];
+    const long long c0 = (long long)blockIdx.x * 64, r0 = (long long)blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 64; i += 8)
+        for (int j = tx; j < 64; j += 32) {
+            const long long r = r0 + i, c = c0 + j;
+            t[i][j] = (r < rows && c < cols) ? in[r * cols + c] : __float2bfloat16(0.f);
+        }
+    __syncthreads();
+    for (int i = ty; i < 64; i += 8)
+        for (int j = tx; j < 64; j += 32) {
+            const long long c = c0 + i, r = r0 + j;
+            if (c < cols && r < rows) out[c * rows + r] = t[j][i];
+        }
+}
+
+cudaError_t transpose_bf16(const __nv_bfloat16* in, long long rows, long long cols, __nv_bfloat16* out,
+                           cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const long long gx = (cols + 63) / 64, gy = (rows + 63) / 64;
+    if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
+    transpose_bf16_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(in, rows, cols, out);
+    return cudaGetLastError();
+}
+
 cudaError_t cast_bf16(const float* x, __nv_bfloat16* y, size_t n, cudaStream_t st)
 {
     cast_kernel<<<blocks_for(n), 256, 0, st>>>(x, y, n);

@@ -51,6 +51,7 @@ def _lib():
             "es_sur_loss_grad": ([vp, vp, vp, vp, ci, ctypes.POINTER(cf), vp, vp], ci),
             "es_sur_train_step": ([vp, vp, vp, vp, ci, cf, ctypes.POINTER(cf)], ci),
             "es_gemm_bf16": ([ci, ci, ci, vp, ci, ci, vp, ci, ci, vp, ci, cf, cf, ci, vp], ci),
+            "es_gemm_status": ([], ci),
             "es_sur_combine": ([vp, ci, ctypes.c_longlong, vp, vp, ci, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
@@ -71,6 +72,12 @@ def _dp(t):
 def _check(rc, where):
     if rc != 0:
         raise _es.EsError(rc, where)
+
+
+def es_gemm_status():
+    """Synchronizes the device; raises EsError if a bounded wait of the
+    tcgen05 GEMM ran out since the last call (es_gemm_status)."""
+    _check(_lib().es_gemm_status(), "es_gemm_status")
 
 
 def es_gemm_bf16(A, B, C, a_t=False, b_nk=False, alpha=1.0, beta=0.0, split_k=1, stream=None):
@@ -219,10 +226,12 @@ def random_moment_tensors(rng, n):
     return out
 
 
-def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=None):
+def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=None, warmup=0.02):
     """Adam on the catalog: every epoch draws per_loc fresh moment tensors per
     location (random_moment_tensors) and regresses the network onto their exact
-    seismograms (combine).  pos_n: [n_loc][3] normalized positions."""
+    seismograms (combine).  pos_n: [n_loc][3] normalized positions.  Learning
+    rate: linear warm-up over the first `warmup` fraction of the steps, then a
+    cosine decay."""
     import torch
     n_loc = G.shape[0]
     sur.fit_output_scale(G.view(n_loc * 6, -1))
@@ -246,6 +255,8 @@ def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=Non
             li = torch.from_numpy(loc[idx]).cuda()
             mm = torch.from_numpy(mts[idx].astype(np.float32)).cuda()
             lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / n_steps))
+            if step < warmup * n_steps:
+                lr_t *= (step + 1) / (warmup * n_steps)
             losses.append(sur.train_step(pos_dev[li].contiguous(), mm, tgt, max(lr_t, 1e-6)))
             step += 1
         history.append(float(np.mean(losses)))

@@ -48,6 +48,34 @@ def test_gemm_all_layouts(env, a_t, b_nk, split):
     assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("M,N,K,split,beta", [(8, 8, 8, 1, 0.0), (128, 256, 64, 1, 0.0), (300, 520, 1000, 1, 1.5),
+                                               (256, 1000, 4608, 6, -0.5), (130, 260, 136, 1, 0.0),
+                                               (64, 4608, 8192, 16, 0.0)])
+def test_tcgen05_gemm_k_major(env, M, N, K, split, beta):
+    """Both operands K-major: the tcgen05 kernel (TMA ring, tensor-memory
+    accumulator), single tiles, ragged edges in M, N and K, split-K."""
+    import ctypes
+    es, sur, torch = env
+    rng = np.random.default_rng(M + N + K + split)
+    lda, ldb, ldc = K + 8, K + 16, N + 4  # leading dimensions past the matrix edge
+    A = rng.standard_normal((M, lda)).astype(np.float32)
+    B = rng.standard_normal((N, ldb)).astype(np.float32)
+    Ab, Bb = _bf(torch, A), _bf(torch, B)
+    A64 = Ab.float().cpu().numpy().astype(np.float64)[:, :K]
+    B64 = Bb.float().cpu().numpy().astype(np.float64)[:, :K]
+    C0 = rng.standard_normal((M, ldc)).astype(np.float32)
+    C = torch.from_numpy(C0.copy()).cuda()
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    rc = sur._lib().es_gemm_bf16(M, N, K, vp(Ab), lda, 0, vp(Bb), ldb, 1, vp(C), ldc, ctypes.c_float(0.75),
+                                 ctypes.c_float(beta), split, None)
+    assert rc == 0
+    sur.es_gemm_status()
+    ref = 0.75 * A64 @ B64.T + beta * C0[:, :N]
+    got = C.cpu().numpy()
+    assert np.abs(got[:, :N] - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert np.array_equal(got[:, N:], C0[:, N:])  # columns past N untouched
+
+
 def test_loss_and_gradients_match_oracle(env):
     es, sur, torch = env
     from oracle import surrogate as osur
