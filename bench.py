@@ -194,7 +194,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate"])
+    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm"])
+    ap.add_argument("--gemm-small", action="store_true", help="gemm workload: the decoder shape only")
     ap.add_argument("--sur-locations", type=int, default=682)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--sur-hidden", type=int, default=768)
@@ -209,6 +210,10 @@ def main():
     args = ap.parse_args()
     if args.workload == "surrogate":
         return measure_surrogate(args)
+    if args.workload == "configs":
+        return measure_configs(args)
+    if args.workload == "gemm":
+        return measure_gemm(args)
     w = workload(args.workload)
     if args.nt:
         w["nt"] = args.nt
@@ -398,6 +403,143 @@ def measure_batched(es, nt, reps, stream):
             "workload": "64 sources on 128^3 + 16 on 96^3 + 8 on 160^3 marine models, one graph, 32x32 receivers"}
 
 
+def gemm_tflops(sur, M, N, K, b_nk, reps=5):
+    """TFLOP/s of es_gemm_bf16 on random BF16 operands (A [M][K]; B [N][K] when b_nk -- the
+    tcgen05 path -- else [K][N], the mma.sync path), CUDA events on the current stream."""
+    import torch
+    A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda").to(torch.bfloat16) if b_nk else \
+        torch.randn(K, N, device="cuda").to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda")
+    sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
+    e1.record()
+    torch.cuda.synchronize()
+    sur.es_gemm_status()
+    return 2.0 * M * N * K * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def measure_gemm(args):
+    """The surrogate's GEMM alone: the decoder product of 256 sources (256 x 262,144 x 4,608,
+    tcgen05), and 8192^3 on the tcgen05 and mma.sync paths."""
+    import torch
+    from paper_1705_04874_gb300 import surrogate as sur
+    torch.cuda.set_device(0)
+    shapes = [("tcgen05_decoder_256x262144x4608", 256, 262144, 4608, True),
+              ("tcgen05_8192", 8192, 8192, 8192, True), ("mma_sync_8192", 8192, 8192, 8192, False)]
+    if args.gemm_small:
+        shapes = shapes[:1]
+    res = {name: round(gemm_tflops(sur, M, N, K, b, reps=args.steps), 1) for name, M, N, K, b in shapes}
+    print(json.dumps({"metric": "TFLOP/s", "gemm": res, "unit": "TFLOP/s", "dtype": "bf16/f32"}))
+    return 0
+
+
+def measure_configs(args):
+    """Per-configuration numbers: the solver on C1 (32^3 two-layer, explosive, 300 steps, 4x4
+    receivers), C2 (128^3 marine, DC 30/60/90, 2000 steps, 32x32 receivers) and 96^3 / 160^3 marine
+    models (1000 steps, 16x16 receivers), device time of whole es_run calls; the FP64 oracle on C1
+    in full and on 2 steps of C3 with 1 core and with every core; and the timed comparison with
+    cuFFT: one time step's 18 staggered derivatives of 256^3 fields by torch.fft R2C / C2R with the
+    multiplier and a PyTorch axpy update (no PML), against the solver's six fused pass kernels."""
+    import torch
+    import oracle
+    from paper_1705_04874_gb300 import es
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    cfgs = [("C1", 32, 6, 300, 4, "two"), ("C2", 128, 10, 2000, 32, "marine"),
+            ("96^3", 96, 10, 1000, 16, "marine"), ("160^3", 160, 10, 1000, 16, "marine")]
+    out = {"solver": {}}
+    oracle.build()
+    for name, n, pml, nt, rx, kind in cfgs:
+        if kind == "two":
+            rho, cp, cs = synth.two_layer_model(n, water_cells=8)
+            mt, pos, f0 = synth.explosive(), (16, 16, 16), 25.0
+        else:
+            rho, cp, cs = synth.marine_model(n, seed=1)
+            box = synth.reservoir_box((n, n, n), pml)
+            mt, pos, f0 = synth.double_couple_sdr(30, 60, 90), tuple((lo + hi) // 2 for lo, hi in box), 30.0
+        dt = 0.3 * 10.0 / float(cp.max())
+        wav = synth.ricker(nt, dt, f0)
+        with es.Model(rho, cp, cs, dx=10.0, pml=pml, stream=stream) as m:
+            rcv = m.seabed_receivers(rx, rx)
+            m.source_set(pos, mt, torch.from_numpy(wav).cuda())
+            rcv_d = torch.from_numpy(rcv).cuda()
+            tr = torch.empty((4, len(rcv), nt), device="cuda")
+
+            def run():
+                m.state_reset()
+                m.run(nt, dt, rcv_d, tr)
+            ms = timed(run, 3)
+        rec = {"grid": n, "time_steps": nt, "receivers": len(rcv), "ms_per_run": round(ms, 3),
+               "Mcell_steps_per_s": round(float(n) ** 3 * nt / (ms * 1e-3) / 1e6, 1)}
+        if name == "C1":
+            t0 = time.perf_counter()
+            oracle.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml,
+                            sources=[dict(kind="moment", pos=pos, m=mt, w=wav)], receivers=rcv)
+            el = time.perf_counter() - t0
+            rec["oracle_full_run_s"] = round(el, 2)
+            rec["oracle_Mcell_steps_per_s"] = round(float(n) ** 3 * nt / el / 1e6, 2)
+            rec["oracle_cores"] = oracle.default_threads()
+        out["solver"][name] = rec
+    w = workload("256")
+    inp = build_inputs(w)
+    v1, el1, _ = oracle_sample(w, inp, 2, nthreads=1)
+    va, ela, ca = oracle_sample(w, inp, 2)
+    out["oracle_C3"] = {"1_core": round(v1, 3), "all_cores": round(va, 3), "cores": ca, "unit": "Mcell-steps/s",
+                        "sample": "2 time steps of the 256^3 workload"}
+    # cuFFT comparison at 256^3
+    n, d = 256, 10.0
+    g = torch.Generator(device="cuda").manual_seed(5)
+    f = torch.randn((n, n, n), device="cuda", generator=g)
+    tgt = torch.zeros_like(f)
+    kap = 2 * np.pi * np.arange(n // 2 + 1) / (n * d)
+    mult = {sh: torch.from_numpy((1j * kap * np.exp(sh * 1j * kap * d / 2)).astype(np.complex64)).cuda()
+            for sh in (1, -1)}
+
+    def cufft_deriv(x, axis, sh):
+        dim = 2 - axis  # axis 0 = x = the last array dimension
+        shp = [1, 1, 1]
+        shp[dim] = n // 2 + 1
+        return torch.fft.irfft(torch.fft.rfft(x, dim=dim) * mult[sh].view(shp), n=n, dim=dim)
+
+    ref = torch.empty_like(f)
+    es.es_derivative(f, 0, d, 1, ref, stream=stream)
+    diff = float((cufft_deriv(f, 0, 1) - ref).norm() / ref.norm())
+
+    def cufft_step():
+        for k in range(18):
+            tgt.add_(cufft_deriv(f, k % 3, 1 if k % 2 else -1), alpha=1e-3)
+    ms_cufft = timed(cufft_step, 5)
+    rho, cp, cs = synth.marine_model(n, seed=1)
+    with es.Model(rho, cp, cs, dx=d, pml=12, stream=stream) as m:
+        m.source_set(inp["pos"], inp["mt"], torch.from_numpy(inp["wav"][:50]).cuda())
+        m.run(50, inp["dt"])
+        ks = m.last_step_kernel_ms()
+    ms_ours = float(sum(ks[:6]))
+    out["cufft_comparison_256"] = {"cufft_18_derivatives_ms": round(ms_cufft, 3), "fused_6_passes_ms": round(ms_ours, 3),
+                                   "speedup": round(ms_cufft / ms_ours, 2), "derivative_rel_diff": float(f"{diff:.2e}"),
+                                   "note": "cuFFT side: R2C, multiply, C2R, axpy per derivative, no PML, no material "
+                                           "coefficients; fused side: the full velocity and stress update with PML"}
+    print(json.dumps({"metric": "Mcell-steps/s", "configs": out, "n_gpus": 1, "dtype": "f32", "data": "synthetic"}))
+    return 0
+
+
 def measure_surrogate(args):
     """Surrogate workload: 96^3 marine model, PML 10, 8 x 8 seabed receivers,
     1024 samples, Ricker 30 Hz; a catalog of 682 Latin-hypercube locations
@@ -478,32 +620,23 @@ def measure_surrogate(args):
     out["pipeline_sources"] = n_pipe
     # throughput of the network's GEMMs: tcgen05 (both operands K-major: inference decoder,
     # dZ), mma.sync (the other storage orders), and the decoder product at the served shape
-    def gemm_tflops(M, N, K, b_nk, reps=5):
-        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
-        B = torch.randn(N, K, device="cuda").to(torch.bfloat16) if b_nk else \
-            torch.randn(K, N, device="cuda").to(torch.bfloat16)
-        C = torch.empty(M, N, device="cuda")
-        sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            sur.es_gemm_bf16(A, B, C, b_nk=b_nk)
-        e1.record()
-        torch.cuda.synchronize()
-        sur.es_gemm_status()
-        return 2.0 * M * N * K * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
     K6 = 6 * args.sur_latent
-    gemm = {"tcgen05_8192": round(gemm_tflops(8192, 8192, 8192, True), 1),
-            "mma_sync_8192": round(gemm_tflops(8192, 8192, 8192, False), 1),
-            f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(256, s.D, K6, True), 1)}
+    gemm = {"tcgen05_8192": round(gemm_tflops(sur, 8192, 8192, 8192, True), 1),
+            "mma_sync_8192": round(gemm_tflops(sur, 8192, 8192, 8192, False), 1),
+            f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(sur, 256, s.D, K6, True), 1)}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
     dec = gemm[f"tcgen05_decoder_256x{s.D}x{K6}"]
+    # the decoder product reads its BF16 weights once (N K 2 bytes), the codes (M K 2) and writes
+    # the FP32 output (M N 4): 254 flop/byte at M = 256, below the bf16 ridge (~290), so HBM bounds it
+    dec_flop = 2.0 * 256 * s.D * K6
+    dec_bytes = 2.0 * s.D * K6 + 2.0 * 256 * K6 + 4.0 * 256 * s.D
+    dec_gbs = dec_bytes / (dec_flop / (dec * 1e12)) / 1e9
     out.update({"solver_seismograms_per_s": round(solver_rate, 2), "surrogate_seismograms_per_s": round(sur_rate, 1),
                 "pipeline_seismograms_per_s": round(pipe_rate, 1),
                 "pipeline_solver_fraction": round(float(used_solver.mean()), 4),
@@ -519,9 +652,12 @@ def measure_surrogate(args):
     print(json.dumps({"metric": "seismograms/s", "value": out["pipeline_seismograms_per_s"],
                       "unit": "4C seismogram sets/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16/f32",
                       "data": "synthetic", "config": {"workload": out["workload"]},
-                      "roofline": {"bound": "tensor", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
-                                   "achieved": dec, "peak": peak, "unit": "TFLOP/s", "frac": round(dec / peak, 4),
-                                   "traffic": None, "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"},
+                      "roofline": {"bound": "hbm", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
+                                   "achieved": round(dec_gbs, 1), "peak": hbm, "unit": "GB/s",
+                                   "frac": round(dec_gbs / hbm, 4), "traffic": None,
+                                   "algorithmic_bytes": dec_bytes, "tflops": dec, "tensor_peak": peak,
+                                   "tensor_frac": round(dec / peak, 4),
+                                   "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
                       "surrogate": out}))
     return 0
 

@@ -3,23 +3,28 @@
 //   C[M][N] = alpha * A[M][K] * B[N][K]^T + beta * C
 // A row-major [M][K] (lda), B row-major [N][K] (ldb), C FP32 row-major (ldc).
 //
-// One CTA per 128 x 256 output tile (x split_k slices of K), 4 warps:
+// Persistent: one CTA per SM walks the 128 x 256 output tiles (x split_k
+// slices of K) with stride gridDim.x, 6 warps:
 //   warp 0, one thread: TMA producer -- 64-wide K slabs of A (128 rows) and
 //       B (256 rows) into a 4-stage ring of 128-byte-swizzled shared tiles,
-//       completion tracked by transaction-count mbarriers;
+//       completion tracked by transaction-count mbarriers; it runs ahead
+//       across tile boundaries;
 //   warp 1, one thread: issues tcgen05.mma (M 128, N 256, K 16; both
-//       operands from shared-memory descriptors) into a 256-column FP32
-//       accumulator in tensor memory; tcgen05.commit frees each stage and,
-//       at the end, signals the epilogue;
-//   warps 0-3: epilogue -- warp w owns TMEM lanes (tile rows) 32w..32w+31,
-//       reads 32 columns at a time with tcgen05.ld and writes
-//       alpha * acc + beta * C (split_k > 1: atomically adds alpha * acc onto
-//       a C that already holds beta * C).
+//       operands from shared-memory descriptors) into one of two 256-column
+//       FP32 accumulators in tensor memory (512 columns); tcgen05.commit
+//       frees each stage and, at the end of a tile, hands the accumulator to
+//       the epilogue;
+//   warps 2-5: epilogue -- warp w owns TMEM lanes (tile rows)
+//       32 (w mod 4) .. +31, reads 32 columns at a time with tcgen05.ld and
+//       writes alpha * acc + beta * C (split_k > 1: atomically adds
+//       alpha * acc onto a C that already holds beta * C), then returns the
+//       accumulator; the next tile's MMAs run in the other one meanwhile.
 // Rows, columns and K past the matrix edge are zero-filled by TMA and masked
 // in the epilogue.  Every mbarrier wait gives up after WAIT_NS of global
 // time, records the role that gave up in a device status word (read and
-// cleared by gemm_tc_status) and lets the CTA finish: TMA copies still in
-// flight are awaited (again bounded) and the tensor memory is always freed.
+// cleared by gemm_tc_status) and lets the CTA finish: the MMAs issued are
+// awaited, TMA copies still in flight are awaited (both bounded) and the
+// tensor memory is always freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -41,8 +46,8 @@ constexpr int A_BYTES = TM * TK * 2;
 constexpr int B_BYTES = TN * TK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack for the 1024-byte swizzle atoms
-constexpr int THREADS = 128;
-constexpr unsigned TMEM_COLS = TN;
+constexpr int THREADS = 192;
+constexpr unsigned TMEM_COLS = 2 * TN;  // two accumulators
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 static_assert(A_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "swizzle atoms must stay 1024-byte aligned");
@@ -53,7 +58,7 @@ static_assert(A_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "swizzle atoms mus
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 
-__device__ unsigned g_tc_status;  // bit 0 producer, bit 1 MMA, bit 2 epilogue, bit 3 drain gave up
+__device__ unsigned g_tc_status;  // bit 0 producer, 1 MMA, 2 epilogue, 3 MMA drain, 4 TMA drain gave up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -95,6 +100,11 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity)
         if (mbar_try(bar, parity)) return true;
         if ((i & 63u) == 0 && global_ns() - t0 > WAIT_NS) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
@@ -151,34 +161,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-                   int nkb, int kb_per, int mt, int ntl, float* __restrict__ C, int ldc, float alpha, float beta,
-                   int atomic)
+                   int nkb, int kb_per, int mt, int ntl, int ntiles, float* __restrict__ C, int ldc, float alpha,
+                   float beta, int atomic)
 {
     extern __shared__ uint8_t dyn[];
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_issued, s_consumed;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (smem_u32(dyn) + 1023u) & ~1023u;
-    int id = blockIdx.x;
-    const int mi = id % mt;
-    id /= mt;
-    const int ni = id % ntl;
-    const int kb0 = (id / ntl) * kb_per;
-    const int nk = min(nkb, kb0 + kb_per) - kb0;  // >= 1: the host sizes the slices
-    const int m0 = mi * TM, n0 = ni * TN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&mma_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_issued = 0;
         s_consumed = 0;
     }
+    __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(TMEM_COLS)
@@ -190,101 +198,145 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (kb / STAGES) & 1;
-            if (!mbar_wait(&empty[s], ph ^ 1)) {
-                atomicOr(&g_tc_status, 1u);
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: every k-block of every tile of this CTA, through the ring
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int mi = t % mt, rest = t / mt;
+                const int ni = rest % ntl, kb0 = (rest / ntl) * kb_per;
+                const int nk = min(nkb, kb0 + kb_per) - kb0;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
+                        atomicOr(&g_tc_status, 1u);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(sa, &mapA, &full[s], (kb0 + kb) * TK, mi * TM);
+                    tma_load_2d(sa + A_BYTES, &mapB, &full[s], (kb0 + kb) * TK, ni * TN);
+                }
             }
-            const uint32_t sa = base + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(sa, &mapA, &full[s], (kb0 + kb) * TK, m0);
-            tma_load_2d(sa + A_BYTES, &mapB, &full[s], (kb0 + kb) * TK, n0);
+            s_issued = it;
         }
-        s_issued = kb;
-    } else if (warp == 1 && lane == 0) {
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (kb / STAGES) & 1;
-            if (!mbar_wait(&full[s], ph)) {
-                atomicOr(&g_tc_status, 2u);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: accumulator b = local tile index mod 2
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+                const int rest = t / mt;
+                const int kb0 = (rest / ntl) * kb_per;
+                const int nk = min(nkb, kb0 + kb_per) - kb0;
+                const int b = lt & 1;
+                if (!mbar_wait(&acc_empty[b], ((lt >> 1) & 1) ^ 1)) {
+                    atomicOr(&g_tc_status, 2u);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * TN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+                        atomicOr(&g_tc_status, 2u);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * STAGE_BYTES;
+                    const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < TK / UK; ++k) {
+                        const uint64_t step = (uint64_t)((k * UK * 2) >> 4);  // 32 bytes along the swizzled row
+                        tc_mma(acc, da + step, db + step, IDESC, (kb | k) != 0);
+                    }
+                    tc_commit(&empty[s]);
+                }
+                if (ok) tc_commit(&acc_full[b]);
+            }
+            s_consumed = it;
+            tc_commit(&mma_done);  // arrives when every MMA issued above has completed
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quarter q = warp mod 4
+        const int q = warp & 3;
+        const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int mi = t % mt, ni = (t / mt) % ntl;
+            const int b = lt & 1;
+            // one lane waits and the warp follows its verdict: tcgen05.ld below needs the whole warp
+            int got = 0;
+            if (lane == 0) got = mbar_wait(&acc_full[b], (lt >> 1) & 1) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) atomicOr(&g_tc_status, 4u);
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = base + s * STAGE_BYTES;
-            const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + A_BYTES);
+            const int row = mi * TM + q * 32 + lane, n0 = ni * TN;
+            float* crow = C + (size_t)row * ldc;
+            for (int c0 = 0; c0 < TN; c0 += 32) {
+                if (n0 + c0 >= N) break;  // uniform over the warp
+                __syncwarp();               // lanes meet again after the row mask below
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + c0), r);
+                if (row >= M) continue;
+                const int ncol = min(32, N - n0 - c0);
+                float* p = crow + n0 + c0;
+                if (vec && ncol == 32) {
 #pragma unroll
-            for (int k = 0; k < TK / UK; ++k) {
-                const uint64_t step = (uint64_t)((k * UK * 2) >> 4);  // 32 bytes along the swizzled row
-                tc_mma(tmem, da + step, db + step, IDESC, (kb | k) != 0);
-            }
-            tc_commit(&empty[s]);
-        }
-        s_consumed = kb;
-        tc_commit(&done);  // arrives when every MMA issued above has completed
-    }
-    __syncwarp();
-
-    const bool got = mbar_wait(&done, 0);
-    if (!got && lane == 0) atomicOr(&g_tc_status, 4u);
-    tc_fence_after();
-    if (got) {
-        const int row = m0 + warp * 32 + lane;
-        float* crow = C + (size_t)row * ldc;
-        const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            if (n0 + c0 >= N) break;  // uniform over the warp
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row >= M) continue;
-            const int ncol = min(32, N - n0 - c0);
-            float* p = crow + n0 + c0;
-            if (vec && ncol == 32) {
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
-                                           alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
-                    float4* q = reinterpret_cast<float4*>(p + j);
-                    if (atomic) {
-                        atomicAdd(q, v);
-                    } else {
-                        if (beta != 0.f) {
-                            const float4 o = *q;
-                            v.x += beta * o.x;
-                            v.y += beta * o.y;
-                            v.z += beta * o.z;
-                            v.w += beta * o.w;
+                    for (int j = 0; j < 32; j += 4) {
+                        float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
+                                               alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
+                        float4* dst = reinterpret_cast<float4*>(p + j);
+                        if (atomic) {
+                            atomicAdd(dst, v);
+                        } else {
+                            if (beta != 0.f) {
+                                const float4 o = *dst;
+                                v.x += beta * o.x;
+                                v.y += beta * o.y;
+                                v.z += beta * o.z;
+                                v.w += beta * o.w;
+                            }
+                            *dst = v;
                         }
-                        *q = v;
                     }
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (j < ncol) {
-                        const float v = alpha * __uint_as_float(r[j]);
-                        if (atomic) atomicAdd(p + j, v);
-                        else p[j] = beta != 0.f ? v + beta * p[j] : v;
+                    for (int j = 0; j < 32; ++j) {
+                        if (j < ncol) {
+                            const float v = alpha * __uint_as_float(r[j]);
+                            if (atomic) atomicAdd(p + j, v);
+                            else p[j] = beta != 0.f ? v + beta * p[j] : v;
+                        }
                     }
                 }
             }
+            // every tcgen05.ld of this warp has completed (tmem_ld32 waits): hand the accumulator back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
 
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (!mbar_wait(&mma_done, 0)) atomicOr(&g_tc_status, 8u);
         // copies issued but never consumed (only after a wait gave up) must land before the CTA exits
-        for (int kb = s_consumed; kb < s_issued; ++kb)
-            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) {
-                atomicOr(&g_tc_status, 8u);
+        for (int it = s_consumed; it < s_issued; ++it)
+            if (!mbar_wait(&full[it % STAGES], (it / STAGES) & 1)) {
+                atomicOr(&g_tc_status, 16u);
                 break;
             }
     }
+    __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -342,16 +394,21 @@ cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, c
     const int kb_per = (nkb + split_k - 1) / split_k;
     split_k = (nkb + kb_per - 1) / kb_per;  // no empty slice
     const int mt = (M + TM - 1) / TM, ntl = (N + TN - 1) / TN;
-    const long long grid = (long long)mt * ntl * split_k;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const long long ntiles = (long long)mt * ntl * split_k;
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+    const long long grid = ntiles < sms ? ntiles : sms;
     if (split_k > 1 && beta != 1.f) {
         cudaError_t e = scale_f32(C, M, N, ldc, beta, st);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, nkb, kb_per, mt, ntl, C, ldc, alpha,
-                                                               beta, split_k > 1 ? 1 : 0);
+    gemm_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, nkb, kb_per, mt, ntl, (int)ntiles,
+                                                               C, ldc, alpha, beta, split_k > 1 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -50,10 +50,12 @@ def test_gemm_all_layouts(env, a_t, b_nk, split):
 
 @pytest.mark.parametrize("M,N,K,split,beta", [(8, 8, 8, 1, 0.0), (128, 256, 64, 1, 0.0), (300, 520, 1000, 1, 1.5),
                                                (256, 1000, 4608, 6, -0.5), (130, 260, 136, 1, 0.0),
-                                               (64, 4608, 8192, 16, 0.0)])
+                                               (64, 4608, 8192, 16, 0.0), (2000, 4000, 200, 1, 0.5),
+                                               (4096, 8192, 64, 1, 0.0)])
 def test_tcgen05_gemm_k_major(env, M, N, K, split, beta):
-    """Both operands K-major: the tcgen05 kernel (TMA ring, tensor-memory
-    accumulator), single tiles, ragged edges in M, N and K, split-K."""
+    """Both operands K-major: the persistent tcgen05 kernel (TMA ring, two
+    tensor-memory accumulators), single tiles, ragged edges in M, N and K,
+    split-K, and grids of 256 and 1024 tiles (several per CTA)."""
     import ctypes
     es, sur, torch = env
     rng = np.random.default_rng(M + N + K + split)
