@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm"])
+    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm", "serve"])
     ap.add_argument("--gemm-small", action="store_true", help="gemm workload: the decoder shape only")
     ap.add_argument("--sur-locations", type=int, default=682)
     ap.add_argument("--sur-epochs", type=int, default=150)
@@ -214,6 +214,8 @@ def main():
         return measure_configs(args)
     if args.workload == "gemm":
         return measure_gemm(args)
+    if args.workload == "serve":
+        return measure_serve(args)
     w = workload(args.workload)
     if args.nt:
         w["nt"] = args.nt
@@ -438,10 +440,48 @@ def measure_gemm(args):
     return 0
 
 
+def measure_serve(args):
+    """Serving cost of the surrogate network alone: the C5 network shape (64 receivers x 1024
+    samples, 3 -> 768 -> 768 -> 768 latent, 9 positional frequencies; 1.21 G parameters) with
+    its initial weights (the cost does not depend on the values), 10,000 random sources in
+    batches of 256 through es_sur_predict.  Metric: seismogram sets per second."""
+    import torch
+    from paper_1705_04874_gb300 import surrogate as sur
+    torch.cuda.set_device(0)
+    s = sur.Surrogate(64, 1024, nfreq=9, hidden=768, latent=768, max_batch=256, seed=1)
+    rng = np.random.default_rng(3)
+    n_src, B = 10000, 256
+    pos = torch.from_numpy(rng.uniform(-1, 1, (n_src + B, 3)).astype(np.float32)).cuda()
+    mt = torch.from_numpy(rng.standard_normal((n_src + B, 6)).astype(np.float32)).cuda()
+    out = torch.empty((B, s.D), device="cuda")
+
+    def serve_all():
+        for b in range(0, n_src, B):
+            s.predict(pos[b:b + B], mt[b:b + B], out)
+    serve_all()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        serve_all()
+    e1.record()
+    torch.cuda.synchronize()
+    sur.es_gemm_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    s.close()
+    n_batches = (n_src + B - 1) // B
+    print(json.dumps({"metric": "seismograms/s", "value": round(n_src / (ms * 1e-3), 1),
+                      "unit": "4C seismogram sets/s (network only)", "ms_per_10k": round(ms, 2),
+                      "batches": n_batches, "dtype": "bf16/f32", "data": "synthetic"}))
+    return 0
+
+
 def measure_configs(args):
     """Per-configuration numbers: the solver on C1 (32^3 two-layer, explosive, 300 steps, 4x4
-    receivers), C2 (128^3 marine, DC 30/60/90, 2000 steps, 32x32 receivers) and 96^3 / 160^3 marine
-    models (1000 steps, 16x16 receivers), device time of whole es_run calls; the FP64 oracle on C1
+    receivers), C2 (128^3 marine, DC 30/60/90, 2000 steps, 32x32 receivers), 96^3 / 160^3 marine
+    models (1000 steps, 16x16 receivers) and the paper's own grid (125 x 75 x 301 cells, 12.5 /
+    12.5 / 10 m, PML 10, 2000 steps, 105 x 55 seabed receivers = every interior x-y point),
+    device time of whole es_run calls; the FP64 oracle on C1
     in full and on 2 steps of C3 with 1 core and with every core; and the timed comparison with
     cuFFT: one time step's 18 staggered derivatives of 256^3 fields by torch.fft R2C / C2R with the
     multiplier and a PyTorch axpy update (no PML), against the solver's six fused pass kernels."""
@@ -462,22 +502,28 @@ def measure_configs(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    cfgs = [("C1", 32, 6, 300, 4, "two"), ("C2", 128, 10, 2000, 32, "marine"),
-            ("96^3", 96, 10, 1000, 16, "marine"), ("160^3", 160, 10, 1000, 16, "marine")]
+    cfgs = [("C1", (32, 32, 32), 6, 300, (4, 4), "two"), ("C2", (128, 128, 128), 10, 2000, (32, 32), "marine"),
+            ("96^3", (96, 96, 96), 10, 1000, (16, 16), "marine"),
+            ("160^3", (160, 160, 160), 10, 1000, (16, 16), "marine"),
+            ("paper grid 125x75x301", (301, 75, 125), 10, 2000, (105, 55), "paper")]
     out = {"solver": {}}
     oracle.build()
-    for name, n, pml, nt, rx, kind in cfgs:
+    for name, shape, pml, nt, (rx, ry), kind in cfgs:
+        d = (12.5, 12.5, 10.0) if kind == "paper" else (10.0, 10.0, 10.0)
         if kind == "two":
-            rho, cp, cs = synth.two_layer_model(n, water_cells=8)
+            rho, cp, cs = synth.two_layer_model(shape[0], water_cells=8)
             mt, pos, f0 = synth.explosive(), (16, 16, 16), 25.0
         else:
-            rho, cp, cs = synth.marine_model(n, seed=1)
-            box = synth.reservoir_box((n, n, n), pml)
+            rho, cp, cs = synth.marine_model(shape=shape, seed=1)
+            box = synth.reservoir_box(shape, pml)
             mt, pos, f0 = synth.double_couple_sdr(30, 60, 90), tuple((lo + hi) // 2 for lo, hi in box), 30.0
-        dt = 0.3 * 10.0 / float(cp.max())
+        dt = 0.3 * min(d) / float(cp.max())
         wav = synth.ricker(nt, dt, f0)
-        with es.Model(rho, cp, cs, dx=10.0, pml=pml, stream=stream) as m:
-            rcv = m.seabed_receivers(rx, rx)
+        n = shape[0] * shape[1] * shape[2]
+        with es.Model(rho, cp, cs, dx=d[0], pml=pml, stream=stream) as m:
+            if kind == "paper":
+                m.set_spacing(*d)
+            rcv = m.seabed_receivers(rx, ry)
             m.source_set(pos, mt, torch.from_numpy(wav).cuda())
             rcv_d = torch.from_numpy(rcv).cuda()
             tr = torch.empty((4, len(rcv), nt), device="cuda")
@@ -486,15 +532,20 @@ def measure_configs(args):
                 m.state_reset()
                 m.run(nt, dt, rcv_d, tr)
             ms = timed(run, 3)
-        rec = {"grid": n, "time_steps": nt, "receivers": len(rcv), "ms_per_run": round(ms, 3),
-               "Mcell_steps_per_s": round(float(n) ** 3 * nt / (ms * 1e-3) / 1e6, 1)}
+        rec = {"grid": list(shape[::-1]), "time_steps": nt, "receivers": len(rcv), "ms_per_run": round(ms, 3),
+               "Mcell_steps_per_s": round(float(n) * nt / (ms * 1e-3) / 1e6, 1)}
+        if kind == "paper":
+            # the paper's per-source times on this grid (2000 samples): K20 ~1313 s, C2075 ~2091 s
+            rec["passes"] = "circulant on all three axes (125, 75, 301 have no FFT plan)"
+            rec["s_per_source"] = round(ms * 1e-3, 3)
+            rec["vs_paper_k20_s_per_source"] = round(1313.0 / (ms * 1e-3), 1)
         if name == "C1":
             t0 = time.perf_counter()
             oracle.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml,
                             sources=[dict(kind="moment", pos=pos, m=mt, w=wav)], receivers=rcv)
             el = time.perf_counter() - t0
             rec["oracle_full_run_s"] = round(el, 2)
-            rec["oracle_Mcell_steps_per_s"] = round(float(n) ** 3 * nt / el / 1e6, 2)
+            rec["oracle_Mcell_steps_per_s"] = round(float(n) * nt / el / 1e6, 2)
             rec["oracle_cores"] = oracle.default_threads()
         out["solver"][name] = rec
     w = workload("256")

@@ -20,9 +20,13 @@
  *   default stream); a call that returns ES_OK into a host buffer has
  *   finished; into a device buffer, it is complete in stream order.
  * - A model is not thread-safe: one thread at a time per model.
- * - Every axis length must be one of 16, 32, 48, 64, 80, 96, 128, 160, 192,
- *   256 (two-stage FFT plans R1 x R2 with R1, R2 in {4,5,6,8,12,16});
- *   anything else is ES_ERR_SIZE.
+ * - Axis lengths run from 3 to 512; anything else is ES_ERR_SIZE.  The
+ *   lengths 16, 32, 48, 64, 80, 96, 128, 160, 192 and 256 take the fused FFT
+ *   passes (two-stage plans R1 x R2, R1, R2 in {4,5,6,8,10,12,16}; along y
+ *   and z only when nx is even); every other length -- odd or non-smooth
+ *   ones such as the paper's 125 x 75 x 301 grid (Sec. III) -- takes the
+ *   circulant passes, which apply the same staggered spectral derivative as
+ *   an exact periodic convolution with O(n) work per element.
  */
 #ifndef ES_H
 #define ES_H

@@ -1,0 +1,220 @@
+// Staggered spectral derivative passes for axis lengths without an FFT plan
+// (odd or non-smooth lengths such as 75, 125 or 301 = 7 * 43, the paper's
+// own grid; Sec. III).  Along a periodic axis the operator
+//   D(+/-) f = IFFT( i kappa exp(+/- i kappa d / 2) FFT(f) )
+// is a real circulant matrix: (D f)_i = sum_j c[(i - j) mod n] f_j with
+// c_l = sum_m H_m exp(2 pi i m l / n), computed once on the host in FP64
+// (es_capi.cu) and rounded to FP32.  This pass applies that convolution
+// directly, with the same field-update epilogues as the FFT passes, so the
+// result equals the FFT pass up to rounding.  Work per element is O(n)
+// instead of O(log n); the pass is compute-bound for long axes.
+//
+// One CTA: a tile of 32 pencils (32 consecutive x for the y and z passes,
+// 32 consecutive x-lines for the x pass) staged in shared memory as
+// [position][pencil] (row stride 33: conflict-free both ways), an output
+// tile of the same shape, the doubled kernel row c in shared memory, 8 warps.
+// Lane = pencil; a warp computes 16 consecutive outputs at a time with the
+// kernel values in a 23-register window over blocks of 8 inputs: 31 shared
+// loads per 128 FMAs.
+// Accesses are scalar and coalesced (32 consecutive floats per warp), so no
+// alignment of nx is assumed; totals take scalar L2 reductions.
+#include "fft_pass.cuh"
+
+namespace es {
+namespace {
+
+constexpr int TP = 32;          // pencils per tile
+constexpr int ROW = TP + 1;     // shared row stride
+constexpr int OB = 16;          // outputs per warp chunk
+constexpr int JB = 8;           // inputs per block
+constexpr int KOFF = 16;        // front padding of the kernel row (the window reaches OB - 1 before it)
+constexpr int CTHREADS = 256;
+
+__host__ __device__ inline int circ_pad(int n) { return (n + OB - 1) / OB * OB; }
+
+// shared floats: input and output tiles [pad(n)][ROW] + kernel row [2 pad(n) + 2 KOFF + OB]
+__host__ __device__ inline size_t circ_smem(int n)
+{
+    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + 2 * (size_t)circ_pad(n) + 2 * KOFF + OB);
+}
+
+// scalar epilogue for one cell (same arithmetic as epilogue_pair)
+__device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos, int x, int y,
+                                             int z, float d, size_t off, size_t soff)
+{
+    if (J.kind == JOB_STORE) {
+        J.tgt[0][off + q] = d;
+        return;
+    }
+    const float dt = p.dt;
+    const bool slab = in_slab(pos, p.n, p.L);
+    const int S = 2 * p.L + 1;
+    if (J.kind == JOB_SINGLE) {
+        float inc = dt * __ldg(J.coef[0] + q) * d;
+        if (slab) {
+            const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
+            const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            inc = split_delta(J.slab[0], soff + si, P, inc);
+        }
+        atomicAdd(J.tgt[0] + off + q, inc);
+    } else {
+        const float lam = __ldg(J.coef[0] + q), mu = __ldg(J.coef[1] + q);
+        const float P = slab ? __ldg(p.pc + pos) : 1.f;
+        const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            float inc = dt * (lam + (t == J.diag ? 2.f * mu : 0.f)) * d;
+            if (slab) inc = split_delta(J.slab[t], soff + si, P, inc);
+            atomicAdd(J.tgt[t] + off + q, inc);
+        }
+    }
+}
+
+// out[i][lane] = sum_j c[(i - j) mod n] tile[j][lane] for i < n; rows j >= n
+// of the tile are zero.  cw[s] = c[(s - KOFF) mod n]: the window of chunk i0
+// and input block jb starts at c[i0 - jb - (JB - 1)], index
+// KOFF + n + i0 - jb - (JB - 1) >= KOFF - (OB - 1) + 1 > 0 since pad(n) - n < OB,
+// and ends below KOFF + n + pad(n) + OB, inside the row.
+__device__ __forceinline__ void circ_convolve(const float* tile, float* out, const float* cw, int n, int warp,
+                                              int lane)
+{
+    const int np = circ_pad(n);
+    for (int g = warp; g < np / OB; g += CTHREADS / 32) {
+        const int i0 = g * OB;
+        float acc[OB];
+#pragma unroll
+        for (int t = 0; t < OB; ++t) acc[t] = 0.f;
+        for (int jb = 0; jb < np; jb += JB) {
+            float xv[JB];
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj) xv[jj] = tile[(jb + jj) * ROW + lane];
+            float w[OB + JB - 1];  // w[s] = c[i0 - jb - (JB - 1) + s]
+            const float* cb = cw + KOFF + n + i0 - jb - (JB - 1);
+#pragma unroll
+            for (int s = 0; s < OB + JB - 1; ++s) w[s] = cb[s];
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj)
+#pragma unroll
+                for (int t = 0; t < OB; ++t) acc[t] = fmaf(w[t - jj + JB - 1], xv[jj], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < OB; ++t)
+            if (i0 + t < n) out[(i0 + t) * ROW + lane] = acc[t];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n, int tid)
+{
+    const int len = 2 * circ_pad(n) + 2 * KOFF + OB;
+    for (int s = tid; s < len; s += CTHREADS) {
+        int k = (s - KOFF) % n;
+        if (k < 0) k += n;
+        cw[s] = __ldg(c + k);
+    }
+}
+
+// y and z passes: blockIdx.x = (tile of 32 consecutive x) x outer x simulation, blockIdx.y = job
+__global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constant__ PassParams p)
+{
+    extern __shared__ float csm[];
+    const int n = p.n, np = circ_pad(n);
+    float* tile = csm;
+    float* out = tile + (size_t)np * ROW;
+    float* cw = out + (size_t)np * ROW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PassJob& J = p.job[blockIdx.y];
+    const int sim = blockIdx.x % p.nsim, t2 = blockIdx.x / p.nsim;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
+    const int ntx = (p.nx + TP - 1) / TP;
+    const int x0 = (t2 % ntx) * TP, outer = t2 / ntx;
+    size_t base0, est;
+    if (p.axis == 1) {
+        base0 = (size_t)x0 + (size_t)p.nx * p.ny * outer;
+        est = (size_t)p.nx;
+    } else {
+        base0 = (size_t)x0 + (size_t)p.nx * outer;
+        est = (size_t)p.nx * p.ny;
+    }
+    load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
+    for (int it = tid; it < np * TP; it += CTHREADS) {
+        const int pos = it / TP, c = it % TP;
+        float v = 0.f;
+        if (pos < n && x0 + c < p.nx) v = __ldg(J.src + off + base0 + c + (size_t)pos * est);
+        tile[pos * ROW + c] = v;
+    }
+    __syncthreads();
+    circ_convolve(tile, out, cw, n, warp, lane);
+    for (int it = tid; it < n * TP; it += CTHREADS) {
+        const int pos = it / TP, c = it % TP;
+        const int x = x0 + c;
+        if (x >= p.nx) continue;
+        const int y = p.axis == 1 ? pos : outer, z = p.axis == 1 ? outer : pos;
+        epilogue_one(p, J, base0 + c + (size_t)pos * est, pos, x, y, z, out[pos * ROW + c], off, soff);
+    }
+}
+
+// x pass: blockIdx.x = (tile of 32 consecutive x-lines, line = y + ny z) x simulation, blockIdx.y = job
+__global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ PassParams p)
+{
+    extern __shared__ float csm[];
+    const int n = p.n, np = circ_pad(n);
+    float* tile = csm;
+    float* out = tile + (size_t)np * ROW;
+    float* cw = out + (size_t)np * ROW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PassJob& J = p.job[blockIdx.y];
+    const int nlines = p.ny * p.nz;
+    const int sim = blockIdx.x % p.nsim;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
+    const int line0 = (blockIdx.x / p.nsim) * TP;
+    const int nl = min(TP, nlines - line0);
+    load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
+    // the tile's lines are one contiguous block of nl * n floats
+    const float* src = J.src + off + (size_t)line0 * n;
+    for (int e = tid; e < np * ROW; e += CTHREADS) tile[e] = 0.f;  // rows and lines past the edges
+    __syncthreads();
+    for (int e = tid; e < nl * n; e += CTHREADS) {
+        const int r = e / n, pos = e % n;
+        tile[pos * ROW + r] = __ldg(src + e);
+    }
+    __syncthreads();
+    circ_convolve(tile, out, cw, n, warp, lane);
+    for (int e = tid; e < nl * n; e += CTHREADS) {
+        const int r = e / n, pos = e % n;
+        const int line = line0 + r;
+        epilogue_one(p, J, (size_t)line * n + pos, pos, pos, line % p.ny, line / p.ny, out[pos * ROW + r], off,
+                     soff);
+    }
+}
+
+}  // namespace
+
+size_t circ_smem_bytes(int n) { return circ_smem(n); }
+
+cudaError_t prepare_circ_kernels()
+{
+    const int maxb = (int)circ_smem(CIRC_MAX_N);
+    cudaError_t e = cudaFuncSetAttribute(circ_strided, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(circ_x, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+}
+
+cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
+{
+    if (p.n < 2 || p.n > CIRC_MAX_N || !p.ckp || !p.ckm) return cudaErrorInvalidValue;
+    const size_t smem = circ_smem(p.n);
+    if (p.axis == 0) {
+        const int lines = p.ny * p.nz;
+        dim3 grid((unsigned)((lines + TP - 1) / TP) * p.nsim, p.njobs);
+        circ_x<<<grid, CTHREADS, smem, st>>>(p);
+    } else {
+        const int ntx = (p.nx + TP - 1) / TP;
+        const int outer = p.axis == 1 ? p.nz : p.ny;
+        dim3 grid((unsigned)(ntx * outer) * p.nsim, p.njobs);
+        circ_strided<<<grid, CTHREADS, smem, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace es

@@ -141,15 +141,28 @@ int ensure_prepared()
     return ES_OK;
 }
 
-bool axis_ok(int n) { int a, b; return plan_radices(n, &a, &b) != 0; }
+// Axis lengths: an FFT plan (pass_kernels.cu), else the circulant pass up to
+// CIRC_MAX_N (circ_pass.cu).  The y and z FFT passes move x-adjacent pairs, so
+// they need an even nx; with an odd nx every axis takes the circulant pass.
+bool fft_plan(int n) { int a, b; return plan_radices(n, &a, &b) != 0; }
+bool axis_ok(int n) { return n >= 3 && n <= CIRC_MAX_N; }
+bool fft_axis(int n, int nx) { return fft_plan(n) && nx % 2 == 0; }
 
-// i kappa exp(sign i kappa d / 2) / n and exp(-2 pi i m / n), in FP64 then rounded
-void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& hp, std::vector<float2>& hm)
+// i kappa exp(sign i kappa d / 2) / n and exp(-2 pi i m / n), in FP64 then
+// rounded; and the circulant kernels of the two staggered derivatives,
+// c_l = sum_m H_m exp(2 pi i m l / n) (real: H is Hermitian, Nyquist included)
+void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& hp, std::vector<float2>& hm,
+                 std::vector<float>* ckp = nullptr, std::vector<float>* ckm = nullptr)
 {
     const double pi = 3.14159265358979323846;
     tw.resize(n);
     hp.resize(n);
     hm.resize(n);
+    std::vector<double> hr[2], hi[2];
+    for (int s = 0; s < 2; ++s) {
+        hr[s].resize(n);
+        hi[s].resize(n);
+    }
     for (int m = 0; m < n; ++m) {
         const double a = 2.0 * pi * (double)m / (double)n;
         tw[m] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
@@ -157,10 +170,24 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
         const double kap = 2.0 * pi * (double)mk / ((double)n * d);
         for (int s = 0; s < 2; ++s) {
             const double ph = (s == 0 ? 0.5 : -0.5) * kap * d;
-            const float2 h = make_float2((float)(-kap * std::sin(ph) / n), (float)(kap * std::cos(ph) / n));
-            (s == 0 ? hp : hm)[m] = h;
+            hr[s][m] = -kap * std::sin(ph) / n;
+            hi[s][m] = kap * std::cos(ph) / n;
+            (s == 0 ? hp : hm)[m] = make_float2((float)hr[s][m], (float)hi[s][m]);
         }
     }
+    if (!ckp || !ckm) return;
+    ckp->resize(n);
+    ckm->resize(n);
+    for (int l = 0; l < n; ++l)
+        for (int s = 0; s < 2; ++s) {
+            double acc = 0.0;
+            for (int m = 0; m < n; ++m) {
+                const long long ml = ((long long)m * l) % n;
+                const double a = 2.0 * pi * (double)ml / (double)n;
+                acc += hr[s][m] * std::cos(a) - hi[s][m] * std::sin(a);
+            }
+            (s == 0 ? *ckp : *ckm)[l] = (float)acc;
+        }
 }
 
 struct Src {
@@ -193,6 +220,7 @@ struct es_model {
     float* mat[NMAT] = {};
     float** d_fields = nullptr;
     float2 *tw[3] = {}, *hp[3] = {}, *hm[3] = {};
+    float *ckp[3] = {}, *ckm[3] = {};  // circulant kernels (axes without an FFT pass)
     float *pc[3] = {}, *ps[3] = {};
     int* d_int = nullptr;  // [0] step counter, [1] current step, [2] non-finite flag
     std::vector<Src> srcs;
@@ -272,6 +300,22 @@ int upload_sources(es_model* m, double dt)
     return ES_OK;
 }
 
+// twiddles, spectral multipliers and (for a circulant axis) the kernels of axis a
+cudaError_t upload_axis_tables(es_model* m, int a)
+{
+    const int n = axis_len(m, a);
+    std::vector<float2> tw, hp, hm;
+    std::vector<float> ckp, ckm;
+    const bool circ = !fft_axis(n, m->nx);
+    axis_tables(n, m->d[a], tw, hp, hm, circ ? &ckp : nullptr, circ ? &ckm : nullptr);
+    cudaError_t e = cudaMemcpy(m->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(m->ckp[a], ckp.data(), n * 4, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(m->ckm[a], ckm.data(), n * 4, cudaMemcpyHostToDevice);
+    return e;
+}
+
 PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
 {
     PassParams p;
@@ -285,6 +329,9 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.tw = m->tw[axis];
     p.hp = m->hp[axis];
     p.hm = m->hm[axis];
+    p.ckp = m->ckp[axis];
+    p.ckm = m->ckm[axis];
+    p.circ = fft_axis(p.n, m->nx) ? 0 : 1;
     p.pc = m->pc[axis];
     p.ps = m->ps[axis];
     p.L = m->L;
@@ -517,7 +564,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     const size_t A = 256;
     auto up = [&](size_t b) { return (b + A - 1) / A * A; };
     size_t bytes = up(n * 4) * NMAT;
-    for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 2 * up(axis_len(m, a) * 4);
+    for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 4 * up(axis_len(m, a) * 4);
     bytes += up(16) + up(NFIELD * sizeof(float*));
     cudaError_t e = cudaMalloc(&m->pool, bytes);
     if (e != cudaSuccess) {
@@ -531,6 +578,8 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         m->tw[a] = (float2*)take(axis_len(m, a) * 8);
         m->hp[a] = (float2*)take(axis_len(m, a) * 8);
         m->hm[a] = (float2*)take(axis_len(m, a) * 8);
+        m->ckp[a] = (float*)take(axis_len(m, a) * 4);
+        m->ckm[a] = (float*)take(axis_len(m, a) * 4);
         m->pc[a] = (float*)take(axis_len(m, a) * 4);
         m->ps[a] = (float*)take(axis_len(m, a) * 4);
     }
@@ -571,13 +620,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
             e = cudaMemcpy(m->mat[which], h.data(), n * 4, cudaMemcpyHostToDevice);
         }
     }
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-        std::vector<float2> tw, hp, hm;
-        axis_tables(axis_len(m, a), m->d[a], tw, hp, hm);
-        e = cudaMemcpy(m->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
-    }
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = upload_axis_tables(m, a);
     for (int k = 0; k < 2 * KPS_MAX && e == cudaSuccess; ++k) e = cudaEventCreate(&m->ev[k]);
     if (e != cudaSuccess) {
         int r = cuda_fail(e, "es_model_create");
@@ -604,12 +647,7 @@ int es_model_set_spacing(es_model* m, double dx, double dy, double dz)
     m->d[0] = dx;
     m->d[1] = dy;
     m->d[2] = dz;
-    for (int a = 0; a < 3; ++a) {
-        std::vector<float2> tw, hp, hm;
-        axis_tables(axis_len(m, a), m->d[a], tw, hp, hm);
-        CK(cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice));
-    }
+    for (int a = 0; a < 3; ++a) CK(upload_axis_tables(m, a));
     return ES_OK;
 }
 
@@ -1004,14 +1042,14 @@ int es_model_autotune(es_model* m, int reps, char* report, int report_len)
         for (int n : lens) {
             int ra[8], rb[8];
             const int nc = plan_candidates(n, ra, rb, 8);
-            if (nc < 2) continue;
+            if (nc < 2 || !fft_axis(n, m->nx)) continue;
             float best = 1e30f;
             int bi = 0;
             for (int c = 0; c < nc && rc == ES_OK; ++c) {
                 plan_select(kind, n, ra[c], rb[c]);
                 float total = 0.f;
                 for (int a = 0; a < 3; ++a) {
-                    if ((kind == 0) != (a == 0) || axis_len(m, a) != n) continue;
+                    if ((kind == 0) != (a == 0) || axis_len(m, a) != n || !fft_axis(n, m->nx)) continue;
                     for (int half = 0; half < 2; ++half) {
                         const PassParams p = make_pass(m, a, half == 1, (float)dt);
                         cudaError_t e = launch_pass(p, m->stream);  // warm-up
@@ -1162,14 +1200,19 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
     int rc = ensure_prepared();
     if (rc != ES_OK) return rc;
     const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const bool circ = !fft_axis(n, nx);
     std::vector<float2> tw, hp, hm;
-    axis_tables(n, d, tw, hp, hm);
+    std::vector<float> ckp, ckm;
+    axis_tables(n, d, tw, hp, hm, circ ? &ckp : nullptr, circ ? &ckm : nullptr);
     float2* tab = nullptr;
-    CK(cudaMalloc(&tab, 3 * n * 8));
+    CK(cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4));
+    float* ck = reinterpret_cast<float*>(tab + 3 * n);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpy(tab, tw.data(), n * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(tab + n, hp.data(), n * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(tab + 2 * n, hm.data(), n * 8, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(ck, ckp.data(), n * 4, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(ck + n, ckm.data(), n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         PassParams p;
         std::memset(&p, 0, sizeof p);
@@ -1183,6 +1226,9 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
         p.tw = tab;
         p.hp = tab + n;
         p.hm = tab + 2 * n;
+        p.ckp = ck;
+        p.ckm = ck + n;
+        p.circ = circ ? 1 : 0;
         p.job[0].src = f;
         p.job[0].tgt[0] = out;
         p.job[0].kind = JOB_STORE;

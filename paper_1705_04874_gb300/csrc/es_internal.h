@@ -39,6 +39,9 @@ struct PassParams {
     const float2* tw;     // tw[m] = exp(-2 pi i m / n)
     const float2* hp;     // i kappa exp(+i kappa d/2) / n
     const float2* hm;     // i kappa exp(-i kappa d/2) / n
+    const float* ckp;     // circulant kernel of D(+) along the axis (lengths without an FFT plan)
+    const float* ckm;     // circulant kernel of D(-)
+    int circ;             // 1: the circulant pass (circ_pass.cu) instead of the FFT pass
     const float* pc;      // PML factors at whole indices along the axis
     const float* ps;      // PML factors at half indices along the axis
     int L;                // PML cells per face (slab width 2L+1, none if 0)
@@ -57,6 +60,11 @@ int plan_current(int kind, int n, int* ra, int* rb);
 int plan_select(int kind, int n, int ra, int rb);
 // Launches one pass (all jobs) along p.axis.  Returns a cudaError_t.
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
+// Longest axis the circulant pass takes (shared tiles of 2 x 32 x pad(n) floats).
+constexpr int CIRC_MAX_N = 512;
+cudaError_t launch_circ(const PassParams& p, cudaStream_t st);
+cudaError_t prepare_circ_kernels();
+size_t circ_smem_bytes(int n);
 // Opts every pass kernel into the shared memory it needs (once per device).
 cudaError_t prepare_pass_kernels();
 

@@ -25,6 +25,7 @@ struct es_sur {
     float *p, *g, *m, *v;  // parameters, gradients, Adam moments (FP32)
     __nv_bfloat16* pb;     // BF16 mirror of the parameters (GEMM operands)
     float* scale;          // [4]
+    float scale_h[4] = {1.f, 1.f, 1.f, 1.f};  // host copy (GEMM alpha of the fused inference output)
     __nv_bfloat16 *X, *H1b, *H2b, *Zb, *dUb, *dAb, *dH2b, *dH1b;
     float *H1, *H2, *A, *U, *dZ, *dA, *dH2, *dH1, *loss, *acc;
     int t = 0;
@@ -58,9 +59,11 @@ int check_batch(const es_sur* s, const void* pos, const void* mt, int B)
     return ES_OK;
 }
 
-// forward through the decoder: s->U = z Wd (normalized units); for inference
-// the decoder product runs K-major on the tcgen05 tensor cores (z WdT^T)
-int forward(es_sur* s, const float* pos, const float* mt, int B, bool infer = false)
+// forward through the decoder: s->U = z Wd (normalized units).  For inference
+// (out != nullptr) the decoder product runs K-major on the tcgen05 tensor cores
+// (z WdT^T), one call per output component writing out[:, c D/4 ...] directly
+// with that component's scale as alpha.
+int forward(es_sur* s, const float* pos, const float* mt, int B, float* out = nullptr)
 {
     const __nv_bfloat16* W1 = s->pb + s->oW1;
     const __nv_bfloat16* W2 = s->pb + s->oW2;
@@ -74,10 +77,12 @@ int forward(es_sur* s, const float* pos, const float* mt, int B, bool infer = fa
     CKS(gemm_bf16(B, s->K, s->H, s->H2b, s->H, false, W3, s->K, false, s->A, s->K, 1.f, 0.f, 1, s->st));
     CKS(sur_bias_act(s->A, s->p + s->ob3, B, s->K, false, nullptr, s->st));
     CKS(sur_outer(mt, s->A, B, s->K, s->Zb, s->st));
-    if (infer)
-        CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT, 6 * s->K, true, s->U, (int)s->D, 1.f,
-                      0.f, 1, s->st));
-    else
+    if (out) {
+        const long long Dc = s->D / 4;
+        for (int c = 0; c < 4; ++c)
+            CKS(gemm_bf16(B, (int)Dc, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT + (size_t)c * Dc * 6 * s->K, 6 * s->K,
+                          true, out + (size_t)c * Dc, (int)s->D, s->scale_h[c], 0.f, 1, s->st));
+    } else
         CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, Wd, (int)s->D, false, s->U, (int)s->D, 1.f, 0.f,
                       1, s->st));
     return ES_OK;
@@ -238,6 +243,7 @@ int es_sur_set_output_scale(es_sur* s, const float* scale4)
         if (!(scale4[c] > 0) || !std::isfinite(scale4[c])) return ES_ERR_ARG;
     CKS(cudaMemcpyAsync(s->scale, scale4, 4 * sizeof(float), cudaMemcpyHostToDevice, s->st));
     CKS(cudaStreamSynchronize(s->st));
+    for (int c = 0; c < 4; ++c) s->scale_h[c] = scale4[c];
     return ES_OK;
 }
 
@@ -269,8 +275,7 @@ int es_sur_predict(es_sur* s, const float* pos, const float* mt, int B, float* o
         CKS(transpose_bf16(s->pb + s->oWd, 6LL * s->K, s->D, s->WdT, s->st));
         s->wdt_ver = s->ver;
     }
-    if ((rc = forward(s, pos, mt, B, true)) != ES_OK) return rc;
-    CKS(sur_scale_out(s->U, s->scale, B, s->D / 4, out, s->st));
+    if ((rc = forward(s, pos, mt, B, out)) != ES_OK) return rc;
     return ES_OK;
 }
 

@@ -112,11 +112,12 @@ cudaError_t prepare_pass_kernels()
 #define ES_PREP(n, a, b) if ((e = prepare_one<a, b>()) != cudaSuccess) return e;
     ES_PLANS(ES_PREP)
 #undef ES_PREP
-    return cudaSuccess;
+    return prepare_circ_kernels();
 }
 
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st)
 {
+    if (p.circ) return launch_circ(p, st);
     int ra = 0, rb = 0;
     if (!plan_current(p.axis == 0 ? 0 : 1, p.n, &ra, &rb)) return cudaErrorInvalidValue;
 #define ES_CASE(n, a, b) if (ra == a && rb == b) return launch_one<a, b>(p, st);

@@ -39,8 +39,6 @@ cudaError_t sur_contract(const float* M6, const float* dZ, int B, int K, float* 
 // null); acc: device scratch of 2 B floats
 cudaError_t sur_loss(const float* U, const float* T, const float* scale, int B, long long Dc, float eps,
                      __nv_bfloat16* dU, float* loss, float* acc, float* per_sample, cudaStream_t st);
-// out = scale[c] U
-cudaError_t sur_scale_out(const float* U, const float* scale, int B, long long Dc, float* out, cudaStream_t st);
 cudaError_t sur_init_normal(float* p, size_t n, float std, unsigned long long seed, cudaStream_t st);
 // ss[c] = sum of squares of component c over n samples [n][4][Dc]
 cudaError_t sur_comp_sumsq(const float* T, int n, long long Dc, float* ss, cudaStream_t st);

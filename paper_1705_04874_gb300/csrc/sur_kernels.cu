@@ -131,13 +131,6 @@ __global__ void loss_grad_kernel(const float* U, const float* T, const float* sc
     for (long long i = threadIdx.x; i < Dc; i += blockDim.x) dU[base + i] = __float2bfloat16(g * (U[base + i] - T[base + i] * inv));
 }
 
-__global__ void scale_out_kernel(const float* U, const float* scale, int B, long long Dc, float* out)
-{
-    const size_t n = (size_t)B * 4 * Dc;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = scale[(i / Dc) % 4] * U[i];
-}
-
 // x ~ N(0, std^2) from a counter-based hash (splitmix64 of seed + index) and Box-Muller
 __global__ void init_normal_kernel(float* p, size_t n, float std, unsigned long long seed)
 {
@@ -283,12 +276,6 @@ cudaError_t sur_loss(const float* U, const float* T, const float* scale, int B, 
     if (e != cudaSuccess) return e;
     loss_sums_kernel<<<dim3(B, 4), 256, 0, st>>>(U, T, scale, Dc, acc);
     loss_grad_kernel<<<dim3(B, 4), 256, 0, st>>>(U, T, scale, B, Dc, eps, acc, dU, loss, per_sample);
-    return cudaGetLastError();
-}
-
-cudaError_t sur_scale_out(const float* U, const float* scale, int B, long long Dc, float* out, cudaStream_t st)
-{
-    scale_out_kernel<<<blocks_for((size_t)B * 4 * Dc), 256, 0, st>>>(U, scale, B, Dc, out);
     return cudaGetLastError();
 }
 

@@ -50,11 +50,13 @@ def test_host_side_argument_checks(lib):
     assert lib.es_model_create(None, None, None, 32, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
     a = np.ones(8, np.float32)
     p = ctypes.c_void_p(a.ctypes.data)
-    assert lib.es_model_create(p, p, p, 33, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_SIZE
+    # axis lengths run from 3 to 512 (FFT passes for the planned lengths, circulant passes otherwise)
+    assert lib.es_model_create(p, p, p, 513, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_SIZE
+    assert lib.es_model_create(p, p, p, 2, 32, 32, 10.0, 0, ctypes.byref(h)) == es.ES_ERR_SIZE
     assert lib.es_model_create(p, p, p, 32, 32, 32, -1.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
     assert lib.es_model_create(p, p, p, 32, 32, 32, 10.0, 15, ctypes.byref(h)) == es.ES_ERR_ARG
     assert lib.es_superpose(None, 1, 1, 1, None, None, None, 0, 0.1, 1, None, None) == es.ES_ERR_ARG
     assert lib.es_derivative(p, 32, 32, 32, 3, 1.0, 1, p, None) == es.ES_ERR_ARG
-    assert lib.es_derivative(p, 30, 32, 32, 0, 1.0, 1, ctypes.c_void_p(a.ctypes.data + 4), None) == es.ES_ERR_SIZE
+    assert lib.es_derivative(p, 600, 32, 32, 0, 1.0, 1, ctypes.c_void_p(a.ctypes.data + 4), None) == es.ES_ERR_SIZE
     assert lib.es_run(None, 10, 0.0, None, 0, None) == es.ES_ERR_ARG
     assert lib.es_kernels_per_step(None) == es.ES_ERR_ARG

@@ -238,7 +238,7 @@ def test_errors_are_reported(es):
             m.run(10, 0.0)
         assert e.value.status == es.ES_ERR_UNSTABLE
     with pytest.raises(es.EsError) as e:
-        es.Model(*synth.two_layer_model(shape=(32, 32, 36)), dx=10.0, pml=4)
+        es.Model(*synth.two_layer_model(shape=(32, 32, 520)), dx=10.0, pml=4)
     assert e.value.status == es.ES_ERR_SIZE
 
 
