@@ -88,6 +88,19 @@ int es_source_set(es_model* m, const int pos[3], const double mt[6], const float
 /* Adds a further moment-tensor source (same meaning as es_source_set). */
 int es_source_add(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw);
 
+/* Adds a moment-tensor source smoothed in the spatial-frequency domain with a
+ * Blackman window, as the paper does to keep a grid-point delta from ringing
+ * in the pseudo-spectral derivatives (Sec. II-A).  Reading: the window is the
+ * product over the axes of W(m) = 0.42 + 0.5 cos(2 pi m / n) + 0.08 cos(4 pi m / n)
+ * on each axis's signed wavenumber bins m (1 at m = 0, 0 at Nyquist); its
+ * inverse transform is exactly the stencil (0.04, 0.25, 0.42, 0.25, 0.04) per
+ * axis, so after the stress half of step n the stress at cell pos + (i, j, k),
+ * |i|, |j|, |k| <= 2, gains M * wavelet[n] * s_i s_j s_k (weights sum to 1).
+ * The paper's initial-value source is nw = 1, wavelet = {1}: the smoothed
+ * stress distribution appears at the first step.  pos +- 2 must lie outside
+ * the PML (each axis at least 5 long), else ES_ERR_ARG. */
+int es_source_add_smoothed(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw);
+
 /* Adds a point force f = (fx, fy, fz) [N]: after the velocity half of step n,
  * v_i at the source index gains dt f_i wavelet[n] / (rho_i dx dy dz), rho_i
  * the density at v_i's staggered point. */

@@ -51,7 +51,29 @@ class Params(ctypes.Structure):
 class Source(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ix", ctypes.c_int), ("iy", ctypes.c_int),
                 ("iz", ctypes.c_int), ("m", ctypes.c_double * 6),
-                ("w", ctypes.POINTER(ctypes.c_double)), ("nw", ctypes.c_int)]
+                ("w", ctypes.POINTER(ctypes.c_double)), ("nw", ctypes.c_int),
+                ("g", ctypes.POINTER(ctypes.c_double))]
+
+
+def blackman_window(n):
+    """Blackman window over the n signed wavenumber bins of an axis (numpy FFT
+    order), 1 at k = 0 and 0 at the Nyquist wavenumber: the classical window
+    0.42 - 0.5 cos(2 pi t) + 0.08 cos(4 pi t) with t = 1/2 + m/n running over
+    the spatial-frequency axis from -Nyquist to +Nyquist."""
+    m = np.fft.fftfreq(n) * n
+    t = 0.5 + m / n
+    return 0.42 - 0.5 * np.cos(2 * np.pi * t) + 0.08 * np.cos(4 * np.pi * t)
+
+
+def smoothed_delta(shape, pos):
+    """The point source smoothed in the spatial-frequency domain (Sec. II-A):
+    3D FFT of the grid-point delta at pos = (ix, iy, iz), times the product of
+    the three axes' Blackman windows, inverse FFT.  [nz][ny][nx] float64."""
+    nz, ny, nx = shape
+    delta = np.zeros(shape)
+    delta[pos[2], pos[1], pos[0]] = 1.0
+    W = blackman_window(nz)[:, None, None] * blackman_window(ny)[None, :, None] * blackman_window(nx)[None, None, :]
+    return np.fft.ifftn(W * np.fft.fftn(delta)).real
 
 
 def _load():
@@ -139,7 +161,8 @@ def simulate(rho, cp, cs, *, dx, dy=None, dz=None, dt, nt, pml=10, pml_alpha0=2.
 
     sources: iterable of dicts {kind: 'moment'|'force', pos: (ix,iy,iz),
     m: 6 moment components (xx yy zz xy xz yz) or 3 force components,
-    w: wavelet samples}."""
+    w: wavelet samples, smooth: True for a moment source smoothed with the
+    Blackman window in the spatial-frequency domain (smoothed_delta)}."""
     rho, cp, cs = _f64(rho), _f64(cp), _f64(cs)
     nz, ny, nx = rho.shape
     dy = dx if dy is None else dy
@@ -155,8 +178,13 @@ def simulate(rho, cp, cs, *, dx, dy=None, dz=None, dt, nt, pml=10, pml_alpha0=2.
         keep.append(w)
         m = list(s["m"]) + [0.0] * (6 - len(s["m"]))
         kind = 0 if s.get("kind", "moment") == "moment" else 1
+        g = ctypes.POINTER(ctypes.c_double)()
+        if kind == 0 and s.get("smooth"):
+            gd = np.ascontiguousarray(smoothed_delta(rho.shape, s["pos"]))
+            keep.append(gd)
+            g = _dp(gd)
         arr[e] = Source(kind, int(s["pos"][0]), int(s["pos"][1]), int(s["pos"][2]),
-                        (ctypes.c_double * 6)(*m), _dp(w), int(w.size))
+                        (ctypes.c_double * 6)(*m), _dp(w), int(w.size), g)
     if receivers is None:
         receivers = np.zeros((0, 3), np.int32)
     rcv = np.ascontiguousarray(receivers, dtype=np.int32).reshape(-1, 3)

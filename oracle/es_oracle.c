@@ -368,6 +368,9 @@ typedef struct {
     double m[6];       /* kind 0: Mxx Myy Mzz Mxy Mxz Myz;  kind 1: fx fy fz */
     const double *w;   /* wavelet, sample n used at step n */
     int nw;
+    const double *g;   /* kind 0 only: NULL = point source at (ix, iy, iz); else a
+                          [nz][ny][nx] spatial distribution (the smoothed source of
+                          Sec. II-A), every cell gaining M_ij w[n] g */
 } orc_source;
 
 /* whether field f sits at a half-index along axis a (R-stagger) */
@@ -550,6 +553,14 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
         for (int e = 0; e < nsrc; ++e) {          /* R-src, moment tensor */
             const orc_source *S = &src[e];
             if (S->kind != 0 || n >= S->nw) continue;
+            if (S->g) {
+                for (int c = 0; c < 6; ++c) {
+                    int f = SXX + c;
+                    int a0 = split[f][0] ? 0 : 1;
+                    for (size_t q = 0; q < (size_t)nx * ny * nz; ++q) split[f][a0][q] += S->m[c] * S->w[n] * S->g[q];
+                }
+                continue;
+            }
             size_t q = IDX(S->ix, S->iy, S->iz);
             for (int c = 0; c < 6; ++c) {
                 int f = SXX + c;

@@ -10,36 +10,63 @@ namespace es {
 // fixed order.  The step counter lives on the device so that one captured
 // step can be replayed: the kernel that runs last in a step (`advance`)
 // publishes the step index to `cur` for the recorder and increments it.
+// The spatial-frequency Blackman window of one axis, W(m) = 0.42 + 0.5 cos(2 pi m / n)
+// + 0.08 cos(4 pi m / n) over the signed wavenumber bins m (1 at m = 0, 0 at the
+// Nyquist bin), has the inverse DFT 0.42 at offset 0, 0.25 at +-1, 0.04 at +-2
+// and 0 elsewhere (n >= 5): the smoothed point source (Sec. II-A) is exactly the
+// product of these three stencils around the source cell.
+__constant__ float c_blackman5[5] = {0.04f, 0.25f, 0.42f, 0.25f, 0.04f};
+
+// One block.  Thread 0 adds the point sources in order (deterministic); then
+// every thread takes (source, stencil cell) pairs of the smoothed sources and
+// adds with reductions (order free only where smoothed stencils of one
+// simulation overlap); then thread 0 advances the step counter.
 __global__ void inject_kernel(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
-                              int* counter, int* cur, int advance)
+                              int nx, int ny, int* counter, int* cur, int advance)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int n = *counter;
-    for (int e = 0; e < nsrc; ++e) {
-        const SourceDev s = src[e];
-        if (s.kind != kind || n >= s.nw) continue;
-        const float w = s.w[n];
-        const long long q = (long long)s.sim * fstride + s.cell;
-        if (kind == 0) {
-            // moment tensor: stress component i gains M_i w[n] (Mxx Myy Mzz Mxy Mxz Myz)
-            for (int c = 0; c < 6; ++c)
-                if (s.m[c] != 0.f) fields[SXX + c][q] += s.m[c] * w;
-        } else {
-            // point force: m[c] = dt f_c / (rho_c dx dy dz), folded on the host
-            for (int c = 0; c < 3; ++c)
-                if (s.m[c] != 0.f) fields[VX + c][q] += s.m[c] * w;
+    if (threadIdx.x == 0) {
+        for (int e = 0; e < nsrc; ++e) {
+            const SourceDev s = src[e];
+            if (s.kind != kind || s.smooth || n >= s.nw) continue;
+            const float w = s.w[n];
+            const long long q = (long long)s.sim * fstride + s.cell;
+            if (kind == 0) {
+                // moment tensor: stress component i gains M_i w[n] (Mxx Myy Mzz Mxy Mxz Myz)
+                for (int c = 0; c < 6; ++c)
+                    if (s.m[c] != 0.f) fields[SXX + c][q] += s.m[c] * w;
+            } else {
+                // point force: m[c] = dt f_c / (rho_c dx dy dz), folded on the host
+                for (int c = 0; c < 3; ++c)
+                    if (s.m[c] != 0.f) fields[VX + c][q] += s.m[c] * w;
+            }
         }
     }
-    if (advance) {
+    __syncthreads();
+    if (kind == 0) {
+        for (int it = threadIdx.x; it < nsrc * 125; it += blockDim.x) {
+            const int e = it / 125, k = it % 125;
+            const SourceDev& s = src[e];
+            if (!s.smooth || s.kind != 0 || n >= s.nw) continue;
+            const int dx = k % 5 - 2, dy = (k / 5) % 5 - 2, dz = k / 25 - 2;
+            const float g = c_blackman5[dx + 2] * c_blackman5[dy + 2] * c_blackman5[dz + 2];
+            const float w = s.w[n] * g;
+            const long long q = (long long)s.sim * fstride + s.cell + dx + (long long)nx * (dy + (long long)ny * dz);
+            for (int c = 0; c < 6; ++c)
+                if (s.m[c] != 0.f) atomicAdd(fields[SXX + c] + q, s.m[c] * w);
+        }
+    }
+    __syncthreads();
+    if (advance && threadIdx.x == 0) {
         *cur = n;
         *counter = n + 1;
     }
 }
 
 cudaError_t launch_inject(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
-                          int* counter, int* cur, int advance, cudaStream_t st)
+                          int nx, int ny, int* counter, int* cur, int advance, cudaStream_t st)
 {
-    inject_kernel<<<1, 32, 0, st>>>(fields, fstride, src, nsrc, kind, counter, cur, advance);
+    inject_kernel<<<1, 256, 0, st>>>(fields, fstride, src, nsrc, kind, nx, ny, counter, cur, advance);
     return cudaGetLastError();
 }
 

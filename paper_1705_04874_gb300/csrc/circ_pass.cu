@@ -14,8 +14,8 @@
 // [position][pencil] (row stride 33: conflict-free both ways), an output
 // tile of the same shape, the doubled kernel row c in shared memory, 8 warps.
 // Lane = pencil; a warp computes 16 consecutive outputs at a time with the
-// kernel values in a 23-register window over blocks of 8 inputs: 31 shared
-// loads per 128 FMAs.
+// kernel values in a 24-register window over blocks of 8 inputs: 8 shared
+// loads plus 6 16-byte broadcast loads per 128 FMAs.
 // Accesses are scalar and coalesced (32 consecutive floats per warp), so no
 // alignment of nx is assumed; totals take scalar L2 reductions.
 #include "fft_pass.cuh"
@@ -27,15 +27,22 @@ constexpr int TP = 32;          // pencils per tile
 constexpr int ROW = TP + 1;     // shared row stride
 constexpr int OB = 16;          // outputs per warp chunk
 constexpr int JB = 8;           // inputs per block
-constexpr int KOFF = 16;        // front padding of the kernel row (the window reaches OB - 1 before it)
+constexpr int KOFF = 16;        // least front padding of the kernel row (the window reaches OB - 1 before it)
+constexpr int WIN = OB + JB;    // kernel window, rounded up to a multiple of 4
 constexpr int CTHREADS = 256;
 
 __host__ __device__ inline int circ_pad(int n) { return (n + OB - 1) / OB * OB; }
 
-// shared floats: input and output tiles [pad(n)][ROW] + kernel row [2 pad(n) + 2 KOFF + OB]
+// front padding of the kernel row for axis length n: KOFF plus what makes every
+// window start KOFF_n + n + i0 - jb - (JB - 1) (i0, jb multiples of 8) a
+// multiple of 4, so the window loads are aligned float4s
+__host__ __device__ inline int circ_koff(int n) { return KOFF + (((JB - 1 - KOFF - n) % 4) + 4) % 4; }
+
+// shared floats: input and output tiles [pad(n)][ROW] + kernel row [2 pad(n) + 2 KOFF + OB + 8]
+__host__ __device__ inline int circ_row_len(int n) { return 2 * circ_pad(n) + 2 * KOFF + OB + 8; }
 __host__ __device__ inline size_t circ_smem(int n)
 {
-    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + 2 * (size_t)circ_pad(n) + 2 * KOFF + OB);
+    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + (size_t)circ_row_len(n));
 }
 
 // scalar epilogue for one cell (same arithmetic as epilogue_pair)
@@ -71,14 +78,15 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
 }
 
 // out[i][lane] = sum_j c[(i - j) mod n] tile[j][lane] for i < n; rows j >= n
-// of the tile are zero.  cw[s] = c[(s - KOFF) mod n]: the window of chunk i0
-// and input block jb starts at c[i0 - jb - (JB - 1)], index
-// KOFF + n + i0 - jb - (JB - 1) >= KOFF - (OB - 1) + 1 > 0 since pad(n) - n < OB,
-// and ends below KOFF + n + pad(n) + OB, inside the row.
+// of the tile are zero.  cw[s] = c[(s - koff) mod n], koff = circ_koff(n) in
+// [KOFF, KOFF + 3]: the window of chunk i0 and input block jb starts at
+// c[i0 - jb - (JB - 1)], index koff + n + i0 - jb - (JB - 1) >= KOFF - (OB - 1) + 1 > 0
+// since pad(n) - n < OB, a multiple of 4, and its WIN entries end at or below
+// koff + n + pad(n) + OB, inside the row (circ_row_len).
 __device__ __forceinline__ void circ_convolve(const float* tile, float* out, const float* cw, int n, int warp,
                                               int lane)
 {
-    const int np = circ_pad(n);
+    const int np = circ_pad(n), koff = circ_koff(n);
     for (int g = warp; g < np / OB; g += CTHREADS / 32) {
         const int i0 = g * OB;
         float acc[OB];
@@ -88,10 +96,16 @@ __device__ __forceinline__ void circ_convolve(const float* tile, float* out, con
             float xv[JB];
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) xv[jj] = tile[(jb + jj) * ROW + lane];
-            float w[OB + JB - 1];  // w[s] = c[i0 - jb - (JB - 1) + s]
-            const float* cb = cw + KOFF + n + i0 - jb - (JB - 1);
+            float w[WIN];  // w[s] = c[i0 - jb - (JB - 1) + s]
+            const float4* cb = reinterpret_cast<const float4*>(cw + koff + n + i0 - jb - (JB - 1));
 #pragma unroll
-            for (int s = 0; s < OB + JB - 1; ++s) w[s] = cb[s];
+            for (int s = 0; s < WIN / 4; ++s) {
+                const float4 v = cb[s];
+                w[4 * s] = v.x;
+                w[4 * s + 1] = v.y;
+                w[4 * s + 2] = v.z;
+                w[4 * s + 3] = v.w;
+            }
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj)
 #pragma unroll
@@ -106,9 +120,9 @@ __device__ __forceinline__ void circ_convolve(const float* tile, float* out, con
 
 __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n, int tid)
 {
-    const int len = 2 * circ_pad(n) + 2 * KOFF + OB;
+    const int len = circ_row_len(n), koff = circ_koff(n);
     for (int s = tid; s < len; s += CTHREADS) {
-        int k = (s - KOFF) % n;
+        int k = (s - koff) % n;
         if (k < 0) k += n;
         cw[s] = __ldg(c + k);
     }

@@ -192,6 +192,7 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
 
 struct Src {
     int kind;
+    int smooth = 0;
     int sim;
     int pos[3];
     double m[6];
@@ -267,6 +268,7 @@ int upload_sources(es_model* m, double dt)
         const Src& s = m->srcs[e];
         SourceDev& d = h[e];
         d.kind = s.kind;
+        d.smooth = s.smooth;
         d.sim = s.sim;
         d.cell = (long long)s.pos[0] + (long long)m->nx * ((long long)s.pos[1] + (long long)m->ny * s.pos[2]);
         d.w = s.d_w;
@@ -401,8 +403,8 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
     }
     if (has_force) {
         mark(true);
-        CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 1, m->d_int, m->d_int + 1, 0,
-                         st));
+        CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 1, m->nx, m->ny, m->d_int,
+                         m->d_int + 1, 0, st));
         mark(false);
         ++k;
     }
@@ -414,8 +416,8 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         ++k;
     }
     mark(true);
-    CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 0, m->d_int, m->d_int + 1, 1,
-                     st));
+    CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 0, m->nx, m->ny, m->d_int,
+                     m->d_int + 1, 1, st));
     mark(false);
     ++k;
     if (n_rcv > 0) {
@@ -673,11 +675,13 @@ int es_model_default_dt(const es_model* m, double* dt)
     return ES_OK;
 }
 
-static int add_source(es_model* m, int kind, const int pos[3], const double* v, int nv, const float* w, int nw)
+static int add_source(es_model* m, int kind, const int pos[3], const double* v, int nv, const float* w, int nw,
+                      int smooth = 0)
 {
     if (!m || !pos || !v || nw < 0 || (nw > 0 && !w)) return ES_ERR_ARG;
+    const int reach = smooth ? 2 : 0;  // a smoothed source reaches 2 cells out
     for (int a = 0; a < 3; ++a)
-        if (pos[a] < m->L || pos[a] > axis_len(m, a) - 2 - m->L) return ES_ERR_ARG;  // outside the PML slabs
+        if (pos[a] - reach < m->L || pos[a] + reach > axis_len(m, a) - 2 - m->L) return ES_ERR_ARG;  // outside the PML slabs
     for (int c = 0; c < nv; ++c)
         if (!std::isfinite(v[c])) return ES_ERR_ARG;
     std::vector<float> h;
@@ -685,6 +689,7 @@ static int add_source(es_model* m, int kind, const int pos[3], const double* v, 
     if (rc != ES_OK) return rc;
     Src s;
     s.kind = kind;
+    s.smooth = smooth;
     s.sim = 0;
     std::memcpy(s.pos, pos, sizeof s.pos);
     for (int c = 0; c < 6; ++c) s.m[c] = c < nv ? v[c] : 0.0;
@@ -766,6 +771,12 @@ int es_source_add(es_model* m, const int pos[3], const double mt[6], const float
 int es_source_add_force(es_model* m, const int pos[3], const double f[3], const float* wavelet, int nw)
 {
     return add_source(m, 1, pos, f, 3, wavelet, nw);
+}
+
+int es_source_add_smoothed(es_model* m, const int pos[3], const double mt[6], const float* wavelet, int nw)
+{
+    if (m && (m->nx < 5 || m->ny < 5 || m->nz < 5)) return ES_ERR_ARG;
+    return add_source(m, 0, pos, mt, 6, wavelet, nw, 1);
 }
 
 int es_state_reset(es_model* m)

@@ -71,6 +71,7 @@ cudaError_t prepare_pass_kernels();
 // ---- auxiliary kernels (aux_kernels.cu) ----
 struct SourceDev {
     int kind;            // 0 moment, 1 force
+    int smooth;          // 1: spread over the 5 x 5 x 5 Blackman stencil (moment sources)
     int sim;             // simulation the source belongs to
     long long cell;      // linear index
     float m[6];          // moment (Mxx Myy Mzz Mxy Mxz Myz) or force scale per component
@@ -79,7 +80,7 @@ struct SourceDev {
 };
 
 cudaError_t launch_inject(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
-                          int* counter, int* cur, int advance, cudaStream_t st);
+                          int nx, int ny, int* counter, int* cur, int advance, cudaStream_t st);
 // rec[n - start][sim][4][n_rcv]
 cudaError_t launch_record(float* const* fields, long long fstride, int nsim, const long long* rcv_cell,
                           int n_rcv, const int* cur, long long start, float* rec, cudaStream_t st);

@@ -56,6 +56,7 @@ def _load():
                 "es_source_set": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_add": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_add_force": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
+                "es_source_add_smoothed": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_clear": ([vp], c_int),
                 "es_batch_set": ([vp, c_int, vp, vp, vp, c_int], c_int),
                 "es_state_reset": ([vp], c_int),
@@ -89,7 +90,7 @@ def _load():
 def exported_symbols():
     """Names the binding expects the library to export."""
     return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream",
-            "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_force",
+            "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_smoothed", "es_source_add_force",
             "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
             "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
             "es_kernels_per_step", "es_model_autotune", "es_fft_plan",
@@ -290,6 +291,11 @@ class Model:
 
     def source_add_force(self, pos, f, wavelet):
         self._src(self._lib.es_source_add_force, pos, f, 3, wavelet)
+
+    def source_add_smoothed(self, pos, mt, wavelet):
+        """Moment source spread over the 5 x 5 x 5 Blackman stencil
+        (es_source_add_smoothed); wavelet [1.0] is an initial-value source."""
+        self._src(self._lib.es_source_add_smoothed, pos, mt, 6, wavelet)
 
     def batch_set(self, pos, mt, wavelets):
         """nb simulations sharing this model, one moment source each:

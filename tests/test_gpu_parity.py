@@ -275,3 +275,62 @@ def test_superpose_device_buffers(es):
     es.es_superpose(torch.from_numpy(tr).cuda(), torch.from_numpy(src).cuda(), torch.from_numpy(amps).cuda(),
                     torch.from_numpy(t0).cuda(), 1e-3, 120, gather=out)
     assert np.array_equal(out.cpu().numpy(), host)
+
+
+# --------------------------------------------------------------------------
+# smoothed point sources (Sec. II-A: Blackman window in the spatial-frequency domain)
+# --------------------------------------------------------------------------
+
+def _run_smoothed(es, orc, rho, cp, cs, *, pml, nt, src, rcv):
+    dt = cfl_dt(cp, 10.0)
+    with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
+        for s in src:
+            if s.get("smooth"):
+                m.source_add_smoothed(s["pos"], s["m"], s["w"])
+            else:
+                m.source_add(s["pos"], s["m"], s["w"])
+        gpu = m.run(nt, dt, rcv)
+        st = m.state_get()
+    ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml, sources=src, receivers=rcv,
+                       state=np.zeros((9,) + rho.shape))
+    return gpu, st, ref
+
+
+def test_smoothed_source_matches_oracle(es, orc):
+    """Double couple smoothed over the 5 x 5 x 5 Blackman stencil plus a
+    point explosion, 32^3 water over rock, 150 steps."""
+    rho, cp, cs = synth.two_layer_model(32, water_cells=8)
+    nt = 150
+    w = synth.ricker(nt, cfl_dt(cp, 10.0), 25.0)
+    rcv = orc.seabed_receivers(cs, 6, 4, 4)
+    src = [dict(kind="moment", pos=(15, 17, 18), m=synth.double_couple_sdr(30, 60, 90), w=w, smooth=True),
+           dict(kind="moment", pos=(20, 12, 22), m=synth.explosive(0.5), w=w)]
+    gpu, st, ref = _run_smoothed(es, orc, rho, cp, cs, pml=6, nt=nt, src=src, rcv=rcv)
+    err = trace_errors(gpu, ref["traces"])
+    assert err.max() < TOL, err.max()
+    for f in range(9):
+        assert rel_l2(st[f], ref["state"][f]) < TOL, f
+
+
+def test_initial_value_source_matches_oracle(es, orc):
+    """The paper's initial-value form: a smoothed stress distribution set at
+    the first step (wavelet = [1]) on an odd 27 x 30 x 33 grid."""
+    rho, cp, cs = synth.two_layer_model(shape=(27, 30, 33), water_cells=6)
+    rcv = orc.seabed_receivers(cs, 4, 3, 3)
+    src = [dict(kind="moment", pos=(16, 15, 15), m=synth.explosive(), w=np.ones(1, np.float32), smooth=True)]
+    gpu, st, ref = _run_smoothed(es, orc, rho, cp, cs, pml=4, nt=80, src=src, rcv=rcv)
+    err = trace_errors(gpu, ref["traces"])
+    assert err.max() < TOL, err.max()
+    for f in range(9):
+        assert rel_l2(st[f], ref["state"][f]) < TOL, f
+
+
+def test_smoothed_source_must_clear_the_pml(es):
+    rho, cp, cs = synth.two_layer_model(32, water_cells=8)
+    w = np.ones(4, np.float32)
+    with es.Model(rho, cp, cs, dx=10.0, pml=6) as m:
+        m.source_add((8, 16, 16), synth.explosive(), w)            # a point source fits at pml + 2
+        with pytest.raises(es.EsError) as e:
+            m.source_add_smoothed((7, 16, 16), synth.explosive(), w)  # its stencil would reach x = 5
+        assert e.value.status == es.ES_ERR_ARG
+        m.source_add_smoothed((8, 16, 16), synth.explosive(), w)
