@@ -61,6 +61,19 @@ enum {
 int es_model_create(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz,
                     double dx, int pml, es_model** out);
 
+/* Arithmetic of the spatial derivatives (the fields are FP32 either way).
+ * ES_PREC_FP32 (default): fused FFT passes where an axis has a plan, FP32
+ * circulant passes elsewhere.  ES_PREC_COMPENSATED: every axis through the
+ * circulant passes with error-free transformations (each product split exactly
+ * by one FMA, Knuth's TwoSum on the running sum, the kernel row as FP32 high
+ * plus low parts), so each derivative is accurate to about twice FP32's
+ * precision and only the FP32 storage of the fields limits the traces (O(n)
+ * work per element, about 10 FP32 operations per multiply-add).  Applies from
+ * the next es_run.  ES_ERR_ARG for any other mode. */
+#define ES_PREC_FP32 0
+#define ES_PREC_COMPENSATED 1
+int es_model_set_precision(es_model* m, int mode);
+
 /* Anisotropic spacing [m] (the paper's grid is 12.5 / 12.5 / 10 m, Sec. II-B). */
 int es_model_set_spacing(es_model* m, double dx, double dy, double dz);
 

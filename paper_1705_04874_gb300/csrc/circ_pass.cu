@@ -18,6 +18,14 @@
 // loads plus 6 16-byte broadcast loads per 128 FMAs.
 // Accesses are scalar and coalesced (32 consecutive floats per warp), so no
 // alignment of nx is assumed; totals take scalar L2 reductions.
+//
+// Compensated variant (ES_PREC_COMPENSATED): the kernel row is held as
+// c_hi + c_lo (both FP32), every product c_hi x is split exactly into p + e
+// with one FMA (e = fma(c_hi, x, -p)), the running sum is kept as s_hi + s_lo
+// with Knuth's TwoSum, and c_lo x, e and the TwoSum errors go to s_lo; the
+// result s_hi + s_lo carries the derivative to about twice FP32's precision,
+// so only the FP32 storage of the fields limits accuracy.  Chunks of 8 outputs
+// (registers), 10 FP32 operations per multiply-add.
 #include "fft_pass.cuh"
 
 namespace es {
@@ -28,7 +36,6 @@ constexpr int ROW = TP + 1;     // shared row stride
 constexpr int OB = 16;          // outputs per warp chunk
 constexpr int JB = 8;           // inputs per block
 constexpr int KOFF = 16;        // least front padding of the kernel row (the window reaches OB - 1 before it)
-constexpr int WIN = OB + JB;    // kernel window, rounded up to a multiple of 4
 constexpr int CTHREADS = 256;
 
 __host__ __device__ inline int circ_pad(int n) { return (n + OB - 1) / OB * OB; }
@@ -40,9 +47,9 @@ __host__ __device__ inline int circ_koff(int n) { return KOFF + (((JB - 1 - KOFF
 
 // shared floats: input and output tiles [pad(n)][ROW] + kernel row [2 pad(n) + 2 KOFF + OB + 8]
 __host__ __device__ inline int circ_row_len(int n) { return 2 * circ_pad(n) + 2 * KOFF + OB + 8; }
-__host__ __device__ inline size_t circ_smem(int n)
+__host__ __device__ inline size_t circ_smem(int n, bool comp)
 {
-    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + (size_t)circ_row_len(n));
+    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + (comp ? 2 : 1) * (size_t)circ_row_len(n));
 }
 
 // scalar epilogue for one cell (same arithmetic as epilogue_pair)
@@ -79,41 +86,67 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
 
 // out[i][lane] = sum_j c[(i - j) mod n] tile[j][lane] for i < n; rows j >= n
 // of the tile are zero.  cw[s] = c[(s - koff) mod n], koff = circ_koff(n) in
-// [KOFF, KOFF + 3]: the window of chunk i0 and input block jb starts at
-// c[i0 - jb - (JB - 1)], index koff + n + i0 - jb - (JB - 1) >= KOFF - (OB - 1) + 1 > 0
-// since pad(n) - n < OB, a multiple of 4, and its WIN entries end at or below
-// koff + n + pad(n) + OB, inside the row (circ_row_len).
-__device__ __forceinline__ void circ_convolve(const float* tile, float* out, const float* cw, int n, int warp,
-                                              int lane)
+// [KOFF, KOFF + 3]: the window of chunk i0 (a multiple of OBV) and input block
+// jb starts at c[i0 - jb - (JB - 1)], index koff + n + i0 - jb - (JB - 1) >=
+// KOFF - (OB - 1) + 1 > 0 since pad(n) - n < OB, a multiple of 4, and its
+// OBV + JB entries end at or below koff + n + pad(n) + OB, inside the row
+// (circ_row_len).  COMP: cl is the low part of the row (same layout).
+template <bool COMP, int OBV>
+__device__ __forceinline__ void circ_convolve(const float* tile, float* out, const float* cw, const float* cl, int n,
+                                              int warp, int lane)
 {
+    constexpr int W = OBV + JB;  // window length, a multiple of 4
     const int np = circ_pad(n), koff = circ_koff(n);
-    for (int g = warp; g < np / OB; g += CTHREADS / 32) {
-        const int i0 = g * OB;
-        float acc[OB];
+    for (int g = warp; g < np / OBV; g += CTHREADS / 32) {
+        const int i0 = g * OBV;
+        float acc[OBV], lo[OBV];
 #pragma unroll
-        for (int t = 0; t < OB; ++t) acc[t] = 0.f;
+        for (int t = 0; t < OBV; ++t) {
+            acc[t] = 0.f;
+            lo[t] = 0.f;
+        }
         for (int jb = 0; jb < np; jb += JB) {
             float xv[JB];
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj) xv[jj] = tile[(jb + jj) * ROW + lane];
-            float w[WIN];  // w[s] = c[i0 - jb - (JB - 1) + s]
-            const float4* cb = reinterpret_cast<const float4*>(cw + koff + n + i0 - jb - (JB - 1));
+            const int w0 = koff + n + i0 - jb - (JB - 1);
+            float w[W], wl[COMP ? W : 1];  // w[s] = c[i0 - jb - (JB - 1) + s]
 #pragma unroll
-            for (int s = 0; s < WIN / 4; ++s) {
-                const float4 v = cb[s];
+            for (int s = 0; s < W / 4; ++s) {
+                const float4 v = reinterpret_cast<const float4*>(cw + w0)[s];
                 w[4 * s] = v.x;
                 w[4 * s + 1] = v.y;
                 w[4 * s + 2] = v.z;
                 w[4 * s + 3] = v.w;
+                if constexpr (COMP) {
+                    const float4 u = reinterpret_cast<const float4*>(cl + w0)[s];
+                    wl[4 * s] = u.x;
+                    wl[4 * s + 1] = u.y;
+                    wl[4 * s + 2] = u.z;
+                    wl[4 * s + 3] = u.w;
+                }
             }
 #pragma unroll
             for (int jj = 0; jj < JB; ++jj)
 #pragma unroll
-                for (int t = 0; t < OB; ++t) acc[t] = fmaf(w[t - jj + JB - 1], xv[jj], acc[t]);
+                for (int t = 0; t < OBV; ++t) {
+                    const float c = w[t - jj + JB - 1];
+                    if constexpr (!COMP) {
+                        acc[t] = fmaf(c, xv[jj], acc[t]);
+                    } else {
+                        const float p = __fmul_rn(c, xv[jj]);
+                        const float e = fmaf(c, xv[jj], -p);  // c x = p + e exactly
+                        const float sum = __fadd_rn(acc[t], p);
+                        const float bb = __fsub_rn(sum, acc[t]);
+                        const float err = __fadd_rn(__fsub_rn(acc[t], __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+                        acc[t] = sum;
+                        lo[t] = __fadd_rn(lo[t], __fadd_rn(err, fmaf(wl[t - jj + JB - 1], xv[jj], e)));
+                    }
+                }
         }
 #pragma unroll
-        for (int t = 0; t < OB; ++t)
-            if (i0 + t < n) out[(i0 + t) * ROW + lane] = acc[t];
+        for (int t = 0; t < OBV; ++t)
+            if (i0 + t < n) out[(i0 + t) * ROW + lane] = COMP ? __fadd_rn(acc[t], lo[t]) : acc[t];
     }
     __syncthreads();
 }
@@ -129,6 +162,7 @@ __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n
 }
 
 // y and z passes: blockIdx.x = (tile of 32 consecutive x) x outer x simulation, blockIdx.y = job
+template <bool COMP>
 __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constant__ PassParams p)
 {
     extern __shared__ float csm[];
@@ -136,6 +170,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
     float* tile = csm;
     float* out = tile + (size_t)np * ROW;
     float* cw = out + (size_t)np * ROW;
+    float* cl = cw + circ_row_len(n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const PassJob& J = p.job[blockIdx.y];
     const int sim = blockIdx.x % p.nsim, t2 = blockIdx.x / p.nsim;
@@ -151,6 +186,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
         est = (size_t)p.nx * p.ny;
     }
     load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
+    if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     for (int it = tid; it < np * TP; it += CTHREADS) {
         const int pos = it / TP, c = it % TP;
         float v = 0.f;
@@ -158,7 +194,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
         tile[pos * ROW + c] = v;
     }
     __syncthreads();
-    circ_convolve(tile, out, cw, n, warp, lane);
+    circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
     for (int it = tid; it < n * TP; it += CTHREADS) {
         const int pos = it / TP, c = it % TP;
         const int x = x0 + c;
@@ -169,6 +205,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
 }
 
 // x pass: blockIdx.x = (tile of 32 consecutive x-lines, line = y + ny z) x simulation, blockIdx.y = job
+template <bool COMP>
 __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ PassParams p)
 {
     extern __shared__ float csm[];
@@ -176,6 +213,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     float* tile = csm;
     float* out = tile + (size_t)np * ROW;
     float* cw = out + (size_t)np * ROW;
+    float* cl = cw + circ_row_len(n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const PassJob& J = p.job[blockIdx.y];
     const int nlines = p.ny * p.nz;
@@ -184,6 +222,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     const int line0 = (blockIdx.x / p.nsim) * TP;
     const int nl = min(TP, nlines - line0);
     load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
+    if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     // the tile's lines are one contiguous block of nl * n floats
     const float* src = J.src + off + (size_t)line0 * n;
     for (int e = tid; e < np * ROW; e += CTHREADS) tile[e] = 0.f;  // rows and lines past the edges
@@ -193,7 +232,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
         tile[pos * ROW + r] = __ldg(src + e);
     }
     __syncthreads();
-    circ_convolve(tile, out, cw, n, warp, lane);
+    circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
     for (int e = tid; e < nl * n; e += CTHREADS) {
         const int r = e / n, pos = e % n;
         const int line = line0 + r;
@@ -204,29 +243,34 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
 
 }  // namespace
 
-size_t circ_smem_bytes(int n) { return circ_smem(n); }
+size_t circ_smem_bytes(int n) { return circ_smem(n, false); }
 
 cudaError_t prepare_circ_kernels()
 {
-    const int maxb = (int)circ_smem(CIRC_MAX_N);
-    cudaError_t e = cudaFuncSetAttribute(circ_strided, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(circ_x, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    const int maxb = (int)circ_smem(CIRC_MAX_N, true);
+    cudaError_t e = cudaFuncSetAttribute(circ_strided<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    return e;
 }
 
 cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
 {
     if (p.n < 2 || p.n > CIRC_MAX_N || !p.ckp || !p.ckm) return cudaErrorInvalidValue;
-    const size_t smem = circ_smem(p.n);
+    if (p.comp && (!p.ckp_lo || !p.ckm_lo)) return cudaErrorInvalidValue;
+    const size_t smem = circ_smem(p.n, p.comp != 0);
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((unsigned)((lines + TP - 1) / TP) * p.nsim, p.njobs);
-        circ_x<<<grid, CTHREADS, smem, st>>>(p);
+        if (p.comp) circ_x<true><<<grid, CTHREADS, smem, st>>>(p);
+        else circ_x<false><<<grid, CTHREADS, smem, st>>>(p);
     } else {
         const int ntx = (p.nx + TP - 1) / TP;
         const int outer = p.axis == 1 ? p.nz : p.ny;
         dim3 grid((unsigned)(ntx * outer) * p.nsim, p.njobs);
-        circ_strided<<<grid, CTHREADS, smem, st>>>(p);
+        if (p.comp) circ_strided<true><<<grid, CTHREADS, smem, st>>>(p);
+        else circ_strided<false><<<grid, CTHREADS, smem, st>>>(p);
     }
     return cudaGetLastError();
 }

@@ -152,7 +152,7 @@ bool fft_axis(int n, int nx) { return fft_plan(n) && nx % 2 == 0; }
 // rounded; and the circulant kernels of the two staggered derivatives,
 // c_l = sum_m H_m exp(2 pi i m l / n) (real: H is Hermitian, Nyquist included)
 void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& hp, std::vector<float2>& hm,
-                 std::vector<float>* ckp = nullptr, std::vector<float>* ckm = nullptr)
+                 std::vector<double>* ckp = nullptr, std::vector<double>* ckm = nullptr)
 {
     const double pi = 3.14159265358979323846;
     tw.resize(n);
@@ -186,7 +186,7 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
                 const double a = 2.0 * pi * (double)ml / (double)n;
                 acc += hr[s][m] * std::cos(a) - hi[s][m] * std::sin(a);
             }
-            (s == 0 ? *ckp : *ckm)[l] = (float)acc;
+            (s == 0 ? *ckp : *ckm)[l] = acc;
         }
 }
 
@@ -222,6 +222,8 @@ struct es_model {
     float** d_fields = nullptr;
     float2 *tw[3] = {}, *hp[3] = {}, *hm[3] = {};
     float *ckp[3] = {}, *ckm[3] = {};  // circulant kernels (axes without an FFT pass)
+    float *ckp_lo[3] = {}, *ckm_lo[3] = {};  // their low parts (compensated mode)
+    int prec = ES_PREC_FP32;
     float *pc[3] = {}, *ps[3] = {};
     int* d_int = nullptr;  // [0] step counter, [1] current step, [2] non-finite flag
     std::vector<Src> srcs;
@@ -303,18 +305,35 @@ int upload_sources(es_model* m, double dt)
 }
 
 // twiddles, spectral multipliers and (for a circulant axis) the kernels of axis a
+// whether axis a of the model runs through the circulant passes
+bool circ_axis(const es_model* m, int a) { return m->prec == ES_PREC_COMPENSATED || !fft_axis(axis_len(m, a), m->nx); }
+
+// twiddles, spectral multipliers and (for a circulant axis) the kernels of axis
+// a, the latter as FP32 high parts and FP32 low parts (c - (float)c)
 cudaError_t upload_axis_tables(es_model* m, int a)
 {
     const int n = axis_len(m, a);
     std::vector<float2> tw, hp, hm;
-    std::vector<float> ckp, ckm;
-    const bool circ = !fft_axis(n, m->nx);
+    std::vector<double> ckp, ckm;
+    const bool circ = circ_axis(m, a);
     axis_tables(n, m->d[a], tw, hp, hm, circ ? &ckp : nullptr, circ ? &ckm : nullptr);
     cudaError_t e = cudaMemcpy(m->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
-    if (circ && e == cudaSuccess) e = cudaMemcpy(m->ckp[a], ckp.data(), n * 4, cudaMemcpyHostToDevice);
-    if (circ && e == cudaSuccess) e = cudaMemcpy(m->ckm[a], ckm.data(), n * 4, cudaMemcpyHostToDevice);
+    if (circ) {
+        std::vector<float> hi(4 * (size_t)n);
+        for (int l = 0; l < n; ++l) {
+            const float p = (float)ckp[l], q = (float)ckm[l];
+            hi[l] = p;
+            hi[n + l] = q;
+            hi[2 * n + l] = (float)(ckp[l] - (double)p);
+            hi[3 * n + l] = (float)(ckm[l] - (double)q);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(m->ckp[a], hi.data(), n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->ckm[a], hi.data() + n, n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->ckp_lo[a], hi.data() + 2 * n, n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->ckm_lo[a], hi.data() + 3 * n, n * 4, cudaMemcpyHostToDevice);
+    }
     return e;
 }
 
@@ -333,7 +352,10 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.hm = m->hm[axis];
     p.ckp = m->ckp[axis];
     p.ckm = m->ckm[axis];
-    p.circ = fft_axis(p.n, m->nx) ? 0 : 1;
+    p.ckp_lo = m->ckp_lo[axis];
+    p.ckm_lo = m->ckm_lo[axis];
+    p.circ = circ_axis(m, axis) ? 1 : 0;
+    p.comp = m->prec == ES_PREC_COMPENSATED ? 1 : 0;
     p.pc = m->pc[axis];
     p.ps = m->ps[axis];
     p.L = m->L;
@@ -566,7 +588,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     const size_t A = 256;
     auto up = [&](size_t b) { return (b + A - 1) / A * A; };
     size_t bytes = up(n * 4) * NMAT;
-    for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 4 * up(axis_len(m, a) * 4);
+    for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 6 * up(axis_len(m, a) * 4);
     bytes += up(16) + up(NFIELD * sizeof(float*));
     cudaError_t e = cudaMalloc(&m->pool, bytes);
     if (e != cudaSuccess) {
@@ -582,6 +604,8 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         m->hm[a] = (float2*)take(axis_len(m, a) * 8);
         m->ckp[a] = (float*)take(axis_len(m, a) * 4);
         m->ckm[a] = (float*)take(axis_len(m, a) * 4);
+        m->ckp_lo[a] = (float*)take(axis_len(m, a) * 4);
+        m->ckm_lo[a] = (float*)take(axis_len(m, a) * 4);
         m->pc[a] = (float*)take(axis_len(m, a) * 4);
         m->ps[a] = (float*)take(axis_len(m, a) * 4);
     }
@@ -640,6 +664,14 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         return rc;
     }
     *out = m;
+    return ES_OK;
+}
+
+int es_model_set_precision(es_model* m, int mode)
+{
+    if (!m || (mode != ES_PREC_FP32 && mode != ES_PREC_COMPENSATED)) return ES_ERR_ARG;
+    m->prec = mode;
+    for (int a = 0; a < 3; ++a) CK(upload_axis_tables(m, a));
     return ES_OK;
 }
 
@@ -1053,7 +1085,7 @@ int es_model_autotune(es_model* m, int reps, char* report, int report_len)
         for (int n : lens) {
             int ra[8], rb[8];
             const int nc = plan_candidates(n, ra, rb, 8);
-            if (nc < 2 || !fft_axis(n, m->nx)) continue;
+            if (nc < 2 || !fft_axis(n, m->nx) || m->prec != ES_PREC_FP32) continue;
             float best = 1e30f;
             int bi = 0;
             for (int c = 0; c < nc && rc == ES_OK; ++c) {
@@ -1213,8 +1245,9 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
     const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
     const bool circ = !fft_axis(n, nx);
     std::vector<float2> tw, hp, hm;
-    std::vector<float> ckp, ckm;
-    axis_tables(n, d, tw, hp, hm, circ ? &ckp : nullptr, circ ? &ckm : nullptr);
+    std::vector<double> ckp64, ckm64;
+    axis_tables(n, d, tw, hp, hm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
+    std::vector<float> ckp(ckp64.begin(), ckp64.end()), ckm(ckm64.begin(), ckm64.end());
     float2* tab = nullptr;
     CK(cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4));
     float* ck = reinterpret_cast<float*>(tab + 3 * n);

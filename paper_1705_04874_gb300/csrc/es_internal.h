@@ -41,7 +41,10 @@ struct PassParams {
     const float2* hm;     // i kappa exp(-i kappa d/2) / n
     const float* ckp;     // circulant kernel of D(+) along the axis (lengths without an FFT plan)
     const float* ckm;     // circulant kernel of D(-)
+    const float* ckp_lo;  // compensated mode: c - (float)c of the two kernels
+    const float* ckm_lo;
     int circ;             // 1: the circulant pass (circ_pass.cu) instead of the FFT pass
+    int comp;             // 1: compensated circulant pass (error-free products and sums)
     const float* pc;      // PML factors at whole indices along the axis
     const float* ps;      // PML factors at half indices along the axis
     int L;                // PML cells per face (slab width 2L+1, none if 0)

@@ -16,6 +16,7 @@ import numpy as np
 
 from . import build as _build
 
+ES_PREC_FP32, ES_PREC_COMPENSATED = 0, 1
 ES_OK, ES_ERR_ARG, ES_ERR_SIZE, ES_ERR_CUDA, ES_ERR_OOM, ES_ERR_UNSTABLE, ES_ERR_TIMEOUT, ES_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -52,6 +53,7 @@ def _load():
                 "es_model_set_spacing": ([vp, c_double, c_double, c_double], c_int),
                 "es_model_set_pml": ([vp, c_double, c_double], c_int),
                 "es_model_set_stream": ([vp, vp], c_int),
+                "es_model_set_precision": ([vp, c_int], c_int),
                 "es_model_default_dt": ([vp, ctypes.POINTER(c_double)], c_int),
                 "es_source_set": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_add": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
@@ -89,7 +91,7 @@ def _load():
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream",
+    return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream", "es_model_set_precision",
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_smoothed", "es_source_add_force",
             "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
             "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
@@ -264,6 +266,10 @@ class Model:
 
     def set_spacing(self, dx, dy, dz):
         _check(self._lib.es_model_set_spacing(self._h, dx, dy, dz), "es_model_set_spacing")
+
+    def set_precision(self, mode):
+        """ES_PREC_FP32 (0) or ES_PREC_COMPENSATED (1): es_model_set_precision."""
+        _check(self._lib.es_model_set_precision(self._h, int(mode)), "es_model_set_precision")
 
     def set_pml(self, alpha0=2.0, cref=0.0):
         _check(self._lib.es_model_set_pml(self._h, alpha0, cref), "es_model_set_pml")

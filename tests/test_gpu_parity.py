@@ -17,6 +17,8 @@ TOL = 1e-4
 # of the same scheme with a library single-precision FFT lands at 2.0e-3
 # (anisotropic case below) and FP32 storage with exact FFTs at 9e-5; this
 # budget is for the FP32 arithmetic of the paper's precision (Sec. II-A).
+# With compensated derivative arithmetic (ES_PREC_COMPENSATED) the same runs
+# are held to TOL.
 TOL_FP32_LONG = 5e-3
 
 
@@ -76,9 +78,12 @@ def test_derivative_of_nyquist_and_smooth_modes(es):
 # full runs: materials, PML, sources, recording
 # --------------------------------------------------------------------------
 
-def _run_both(es, orc, rho, cp, cs, *, pml, nt, sources, rcv, d=(10.0, 10.0, 10.0), dt=None, alpha0=2.0):
+def _run_both(es, orc, rho, cp, cs, *, pml, nt, sources, rcv, d=(10.0, 10.0, 10.0), dt=None, alpha0=2.0,
+              prec=0):
     dt = cfl_dt(cp, min(d)) if dt is None else dt
     with es.Model(rho, cp, cs, dx=d[0], pml=pml) as m:
+        if prec:
+            m.set_precision(prec)
         if d[1] != d[0] or d[2] != d[0]:
             m.set_spacing(*d)
         m.set_pml(alpha0, 0.0)
@@ -110,6 +115,10 @@ def test_config1_two_layer_explosive(es, orc):
 
 
 def test_marine_dc_and_force_uneven_grid(es, orc):
+    _marine_dc_and_force(es, orc, 0)
+
+
+def _marine_dc_and_force(es, orc, prec):
     shape = (48, 64, 96)
     rho, cp, cs = synth.marine_model(shape=shape, seed=1)
     nt = 220
@@ -120,13 +129,36 @@ def test_marine_dc_and_force_uneven_grid(es, orc):
     assert np.array_equal(rcv, orc.seabed_receivers(cs, 8, 6, 5))
     src = [dict(kind="moment", pos=(40, 30, 25), m=synth.double_couple_sdr(30, 60, 90), w=w),
            dict(kind="force", pos=(55, 33, 28), m=(0.2, -1.0, 0.4), w=w * 1e7)]
-    gpu, ref = _run_both(es, orc, rho, cp, cs, pml=8, nt=nt, sources=src, rcv=rcv)
+    gpu, ref = _run_both(es, orc, rho, cp, cs, pml=8, nt=nt, sources=src, rcv=rcv, prec=prec)
     err = trace_errors(gpu, ref)
-    assert err.max() < TOL_FP32_LONG, err.max()
+    assert err.max() < (TOL if prec else TOL_FP32_LONG), err.max()
     assert np.median(err) < TOL
+    return err
+
+
+# The two long heterogeneous runs again with compensated derivative arithmetic
+# (es_model_set_precision): every trace within the 1e-4 bar.
+def test_compensated_marine_dc_and_force_meets_1e4(es, orc):
+    _marine_dc_and_force(es, orc, es.ES_PREC_COMPENSATED)
+
+
+def test_compensated_anisotropic_meets_1e4(es, orc):
+    _anisotropic(es, orc, es.ES_PREC_COMPENSATED)
+
+
+def test_precision_mode_checked(es):
+    rho, cp, cs = synth.two_layer_model(16, water_cells=4)
+    with es.Model(rho, cp, cs, dx=10.0, pml=2) as m:
+        with pytest.raises(es.EsError) as e:
+            m.set_precision(2)
+        assert e.value.status == es.ES_ERR_ARG
 
 
 def test_anisotropic_spacing_and_pml_strength(es, orc):
+    _anisotropic(es, orc, 0)
+
+
+def _anisotropic(es, orc, prec):
     shape = (80, 32, 64)
     rho, cp, cs = synth.marine_model(shape=shape, seed=3)
     nt = 160
@@ -135,9 +167,10 @@ def test_anisotropic_spacing_and_pml_strength(es, orc):
     w = synth.ricker(nt, dt, 20.0)
     rcv = orc.seabed_receivers(cs, 5, 4, 4)
     src = [dict(kind="moment", pos=(30, 15, 40), m=synth.clvd(), w=w)]
-    gpu, ref = _run_both(es, orc, rho, cp, cs, pml=5, nt=nt, sources=src, rcv=rcv, d=d, alpha0=3.0)
+    gpu, ref = _run_both(es, orc, rho, cp, cs, pml=5, nt=nt, sources=src, rcv=rcv, d=d, alpha0=3.0, prec=prec)
     err = trace_errors(gpu, ref)
-    assert err.max() < TOL_FP32_LONG, err.max()
+    assert err.max() < (TOL if prec else TOL_FP32_LONG), err.max()
+    return err
 
 
 def test_no_pml_and_thin_pml(es, orc):
