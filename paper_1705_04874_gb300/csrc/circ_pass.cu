@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
         base0 = (size_t)x0 + (size_t)p.nx * outer;
         est = (size_t)p.nx * p.ny;
     }
+    pdl_begin(p.pdl);
     load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
     if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     for (int it = tid; it < np * TP; it += CTHREADS) {
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
     }
     __syncthreads();
     circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
+    if (p.pdl == 1) pdl_wait();
     for (int it = tid; it < n * TP; it += CTHREADS) {
         const int pos = it / TP, c = it % TP;
         const int x = x0 + c;
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const int line0 = (blockIdx.x / p.nsim) * TP;
     const int nl = min(TP, nlines - line0);
+    pdl_begin(p.pdl);
     load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
     if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     // the tile's lines are one contiguous block of nl * n floats
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     }
     __syncthreads();
     circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
+    if (p.pdl == 1) pdl_wait();
     for (int e = tid; e < nl * n; e += CTHREADS) {
         const int r = e / n, pos = e % n;
         const int line = line0 + r;
@@ -263,16 +267,12 @@ cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((unsigned)((lines + TP - 1) / TP) * p.nsim, p.njobs);
-        if (p.comp) circ_x<true><<<grid, CTHREADS, smem, st>>>(p);
-        else circ_x<false><<<grid, CTHREADS, smem, st>>>(p);
-    } else {
-        const int ntx = (p.nx + TP - 1) / TP;
-        const int outer = p.axis == 1 ? p.nz : p.ny;
-        dim3 grid((unsigned)(ntx * outer) * p.nsim, p.njobs);
-        if (p.comp) circ_strided<true><<<grid, CTHREADS, smem, st>>>(p);
-        else circ_strided<false><<<grid, CTHREADS, smem, st>>>(p);
+        return launch_pass_kernel(p.comp ? circ_x<true> : circ_x<false>, grid, CTHREADS, smem, st, p);
     }
-    return cudaGetLastError();
+    const int ntx = (p.nx + TP - 1) / TP;
+    const int outer = p.axis == 1 ? p.nz : p.ny;
+    dim3 grid((unsigned)(ntx * outer) * p.nsim, p.njobs);
+    return launch_pass_kernel(p.comp ? circ_strided<true> : circ_strided<false>, grid, CTHREADS, smem, st, p);
 }
 
 }  // namespace es

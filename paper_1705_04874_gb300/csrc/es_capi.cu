@@ -19,6 +19,7 @@
 #include <new>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <sys/stat.h>
@@ -67,6 +68,24 @@ int fetch(const T* src, size_t n, std::vector<T>& out, cudaStream_t st)
         std::memcpy(out.data(), src, n * sizeof(T));
     }
     return ES_OK;
+}
+
+// Runs f(lo, hi) over [0, n) split into contiguous blocks of at least `grain`
+// items on the host's cores (model setup: per-cell FP64 material math, no
+// shared writes between blocks).
+template <class F>
+void parallel_for(size_t n, F f, size_t grain = 1)
+{
+    const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    const size_t nt = std::min<size_t>(hw, std::max<size_t>(1, n / std::max<size_t>(1, grain)));
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (size_t t = 0; t < nt; ++t) th.emplace_back(f, n * t / nt, n * (t + 1) / nt);
+    for (auto& x : th) x.join();
 }
 
 int g_prepared_dev = -1;
@@ -418,6 +437,7 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
     for (int a = 0; a < 3; ++a) {
         PassParams p = make_pass(m, a, false, dt);
+        p.pdl = a == 0 ? 2 : 1;  // the x pass reads what the stress half wrote; y and z only add after it
         mark(true);
         CK(launch_pass(p, st));
         mark(false);
@@ -432,6 +452,7 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
     }
     for (int a = 0; a < 3; ++a) {
         PassParams p = make_pass(m, a, true, dt);
+        p.pdl = a == 0 ? 2 : 1;
         mark(true);
         CK(launch_pass(p, st));
         mark(false);
@@ -565,12 +586,24 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     if ((rc = fetch(cp, n, h_cp, nullptr)) != ES_OK) return rc;
     if ((rc = fetch(cs, n, h_cs, nullptr)) != ES_OK) return rc;
     float cpmax = 0.f;
-    for (size_t q = 0; q < n; ++q) {
-        const float r = h_rho[q], p = h_cp[q], s = h_cs[q];
-        if (!(r > 0.f) || !(p > 0.f) || !(s >= 0.f) || !std::isfinite(r) || !std::isfinite(p) || !std::isfinite(s))
-            return ES_ERR_ARG;
-        if ((double)p * p - 2.0 * (double)s * s < 0.0) return ES_ERR_ARG;  // lambda >= 0
-        cpmax = std::max(cpmax, p);
+    {
+        std::vector<float> bmax(64, 0.f);
+        std::vector<char> bad(64, 0);
+        const size_t nb = 64;
+        parallel_for(nb, [&](size_t b0, size_t b1) {
+            for (size_t b = b0; b < b1; ++b)
+                for (size_t q = n * b / nb; q < n * (b + 1) / nb; ++q) {
+                    const float r = h_rho[q], p = h_cp[q], s = h_cs[q];
+                    if (!(r > 0.f) || !(p > 0.f) || !(s >= 0.f) || !std::isfinite(r) || !std::isfinite(p) ||
+                        !std::isfinite(s) || (double)p * p - 2.0 * (double)s * s < 0.0)  // lambda >= 0
+                        bad[b] = 1;
+                    bmax[b] = std::max(bmax[b], p);
+                }
+        });
+        for (size_t b = 0; b < nb; ++b) {
+            if (bad[b]) return ES_ERR_ARG;
+            cpmax = std::max(cpmax, bmax[b]);
+        }
     }
     es_model* m = new (std::nothrow) es_model();
     if (!m) return ES_ERR_OOM;
@@ -617,15 +650,18 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         std::vector<float> h(n);
         auto idx = [&](int i, int j, int k) { return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k); };
         std::vector<double> mu(n), lam(n);
-        for (size_t q = 0; q < n; ++q) {
-            mu[q] = (double)h_cs[q] * h_cs[q] * h_rho[q];
-            lam[q] = (double)h_cp[q] * h_cp[q] * h_rho[q] - 2.0 * mu[q];
-        }
+        parallel_for(n, [&](size_t q0, size_t q1) {
+            for (size_t q = q0; q < q1; ++q) {
+                mu[q] = (double)h_cs[q] * h_cs[q] * h_rho[q];
+                lam[q] = (double)h_cp[q] * h_cp[q] * h_rho[q] - 2.0 * mu[q];
+            }
+        }, 65536);
         auto hmean = [](double a, double b, double c, double d) {
             return (a == 0.0 || b == 0.0 || c == 0.0 || d == 0.0) ? 0.0 : 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d);
         };
         for (int which = 0; which < NMAT && e == cudaSuccess; ++which) {
-            for (int k = 0; k < nz; ++k)
+            parallel_for((size_t)nz, [&](size_t k0, size_t k1) {
+            for (int k = (int)k0; k < (int)k1; ++k)
                 for (int j = 0; j < ny; ++j)
                     for (int i = 0; i < nx; ++i) {
                         const size_t q = idx(i, j, k);
@@ -643,6 +679,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
                         }
                         h[q] = (float)v;
                     }
+            });
             e = cudaMemcpy(m->mat[which], h.data(), n * 4, cudaMemcpyHostToDevice);
         }
     }

@@ -45,6 +45,8 @@ struct PassParams {
     const float* ckm_lo;
     int circ;             // 1: the circulant pass (circ_pass.cu) instead of the FFT pass
     int comp;             // 1: compensated circulant pass (error-free products and sums)
+    int pdl;              // programmatic dependent launch: 0 off; 1 sources may be read before the
+                          // previous pass finishes (the epilogue waits); 2 wait before any read
     const float* pc;      // PML factors at whole indices along the axis
     const float* ps;      // PML factors at half indices along the axis
     int L;                // PML cells per face (slab width 2L+1, none if 0)

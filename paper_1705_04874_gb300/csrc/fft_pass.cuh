@@ -397,6 +397,44 @@ __host__ __device__ constexpr int pass_min_blocks()
 template <int RA, int RB, int CPAD>
 __host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * ((size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
 
+// Programmatic dependent launch (a pass launched with PDL while the previous
+// pass of the same half-step drains): let the next pass launch once every CTA
+// of this one has started, and wait for the previous pass to complete (and its
+// writes to be visible) before touching what it writes.  Both are no-ops for a
+// plain launch.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Start of a pass.  pdl 2: wait for the previous kernel first, and only then
+// let dependents launch, so a dependent that reads early never overtakes a
+// kernel this one still waits for.  pdl 1: this pass's early reads are final
+// already (it launched after the previous pass had passed its own wait), so
+// dependents may launch at once; the epilogue waits (pdl_wait) before adding.
+// pdl 0: a plain launch, dependents launch when it completes.
+__device__ __forceinline__ void pdl_begin(int pdl)
+{
+    if (pdl == 2) pdl_wait();
+    if (pdl != 0) pdl_launch_dependents();
+}
+
+// Launch of a pass kernel, with the programmatic-stream-serialization
+// attribute when p.pdl is set (the kernel then waits as p.pdl says).
+template <class K>
+inline cudaError_t launch_pass_kernel(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                                      const PassParams& p)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = p.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
 // warm L2 with a 128-byte line the epilogue will read (no registers held)
 __device__ __forceinline__ void prefetch_l2(const void* p)
 {
@@ -430,6 +468,7 @@ pass_strided(const __grid_constant__ PassParams p)
     const int tid = threadIdx.x;
     const int c = tid % CP, j = tid / CP;
     const PassJob& J = p.job[blockIdx.y];
+    pdl_begin(p.pdl);
     // simulations run fastest in blockIdx.x: the CTAs of one tile are adjacent
     // and read that tile's material rows through L2
     const int sim = blockIdx.x % p.nsim, tile = blockIdx.x / p.nsim;
@@ -473,6 +512,7 @@ pass_strided(const __grid_constant__ PassParams p)
     __syncthreads();
     C::stageA_inv(buf, s_tw, a, j, c);
     if (!valid) return;
+    if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
 #pragma unroll
     for (int q = 0; q < RA; ++q) {
         const int pos = j + q * BA;
@@ -500,6 +540,7 @@ pass_x(const __grid_constant__ PassParams p)
     const int tid = threadIdx.x;
     const int c = tid % CP, j = tid / CP;
     const PassJob& J = p.job[blockIdx.y];
+    pdl_begin(p.pdl);
     const int nlines = p.ny * p.nz;
     const int sim = blockIdx.x % p.nsim;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
@@ -548,6 +589,7 @@ pass_x(const __grid_constant__ PassParams p)
 #pragma unroll
     for (int q = 0; q < RA; ++q) buf[(j + q * BA) * CPAD + c] = a[q];
     __syncthreads();
+    if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
 #pragma unroll 4
     for (int it = tid; it < ITEMS; it += NT) {
         const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;

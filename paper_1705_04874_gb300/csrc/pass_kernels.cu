@@ -86,14 +86,12 @@ static cudaError_t launch_one(const PassParams& p, cudaStream_t st)
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((lines + 2 * CP - 1) / (2 * CP) * p.nsim, p.njobs);
-        pass_x<RA, RB><<<grid, threads, pass_smem<RA, RB, CP + 1>(), st>>>(p);
-    } else {
-        const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
-        const int outer = p.axis == 1 ? p.nz : p.ny;
-        dim3 grid(ntx * outer * p.nsim, p.njobs);
-        pass_strided<RA, RB><<<grid, threads, pass_smem<RA, RB, CP>(), st>>>(p);
+        return launch_pass_kernel(pass_x<RA, RB>, grid, threads, pass_smem<RA, RB, CP + 1>(), st, p);
     }
-    return cudaGetLastError();
+    const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
+    const int outer = p.axis == 1 ? p.nz : p.ny;
+    dim3 grid(ntx * outer * p.nsim, p.njobs);
+    return launch_pass_kernel(pass_strided<RA, RB>, grid, threads, pass_smem<RA, RB, CP>(), st, p);
 }
 
 template <int RA, int RB>
