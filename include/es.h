@@ -219,6 +219,15 @@ int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv);
 int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out,
                   void* stream);
 
+/* Laplacian of a field (Sec. VI-A, Eq. (8): the paper thresholds the Laplacian
+ * of the density to pick event locations on rock interfaces):
+ * out = sum over the axes of D(+) D(-) f, which multiplies every wavenumber
+ * bin by -kappa^2 (Nyquist included): the spectral Laplacian, with the
+ * solver's own derivative passes.  f, out: [nz][ny][nx] device arrays
+ * (distinct), spacings dx, dy, dz > 0.  Allocates 2 n floats of scratch. */
+int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, double dz, float* out,
+                 void* stream);
+
 /* FFT plan autotuner: for each axis length of this model with more than one
  * two-stage plan (radix order R1 x R2), times the model's own velocity and
  * stress passes (reps launches after one warm-up, CUDA events on the model's

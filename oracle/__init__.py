@@ -65,6 +65,19 @@ def blackman_window(n):
     return 0.42 - 0.5 * np.cos(2 * np.pi * t) + 0.08 * np.cos(4 * np.pi * t)
 
 
+def laplacian(f, d):
+    """Spectral Laplacian (Sec. VI-A, Eq. (8)): inverse FFT of
+    -(kx^2 + ky^2 + kz^2) times the 3D FFT of f [nz][ny][nx], kappa_m =
+    2 pi m / (n d_axis) on the signed bins; d = (dx, dy, dz).  float64."""
+    f = np.asarray(f, np.float64)
+    nz, ny, nx = f.shape
+    kx = 2 * np.pi * np.fft.fftfreq(nx, d[0])
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d[1])
+    kz = 2 * np.pi * np.fft.fftfreq(nz, d[2])
+    k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    return np.fft.ifftn(-k2 * np.fft.fftn(f)).real
+
+
 def smoothed_delta(shape, pos):
     """The point source smoothed in the spatial-frequency domain (Sec. II-A):
     3D FFT of the grid-point delta at pos = (ix, iy, iz), times the product of

@@ -2,6 +2,8 @@
 // (Sec. II-A: point sources at grid points), 4C receiver recording
 // (Sec. II-A, Eq. (3); Sec. II-B), superposition of single-event traces
 // (Sec. IV), a non-finite scan and slab initialisation.
+#include <algorithm>
+
 #include "es_internal.h"
 
 namespace es {
@@ -67,6 +69,19 @@ cudaError_t launch_inject(float* const* fields, long long fstride, const SourceD
                           int nx, int ny, int* counter, int* cur, int advance, cudaStream_t st)
 {
     inject_kernel<<<1, 256, 0, st>>>(fields, fstride, src, nsrc, kind, nx, ny, counter, cur, advance);
+    return cudaGetLastError();
+}
+
+__global__ void fill_kernel(float* p, size_t n, float v)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+cudaError_t launch_fill(float* p, size_t n, float v, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n, v);
     return cudaGetLastError();
 }
 

@@ -534,6 +534,57 @@ int run_checked_args(es_model* m, int nt, double dt, int n_rcv)
     return ES_OK;
 }
 
+// One staggered derivative of a plain [nz][ny][nx] array along `axis`, with
+// its own tables: out = D f (acc == nullptr) or out += acc * D f (acc: a
+// per-cell coefficient array, e.g. ones).  Stream-ordered; tables freed after
+// the stream reaches them.
+cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out,
+                            const float* acc, cudaStream_t st)
+{
+    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const bool circ = !fft_axis(n, nx);
+    std::vector<float2> tw, hp, hm;
+    std::vector<double> ckp64, ckm64;
+    axis_tables(n, d, tw, hp, hm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
+    std::vector<float> ckp(ckp64.begin(), ckp64.end()), ckm(ckm64.begin(), ckm64.end());
+    float2* tab = nullptr;
+    cudaError_t e = cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4);
+    if (e != cudaSuccess) return e;
+    float* ck = reinterpret_cast<float*>(tab + 3 * n);
+    e = cudaMemcpy(tab, tw.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tab + n, hp.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(tab + 2 * n, hm.data(), n * 8, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(ck, ckp.data(), n * 4, cudaMemcpyHostToDevice);
+    if (circ && e == cudaSuccess) e = cudaMemcpy(ck + n, ckm.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        PassParams p;
+        std::memset(&p, 0, sizeof p);
+        p.nx = nx;
+        p.ny = ny;
+        p.nz = nz;
+        p.axis = axis;
+        p.n = n;
+        p.njobs = 1;
+        p.nsim = 1;
+        p.dt = 1.f;
+        p.tw = tab;
+        p.hp = tab + n;
+        p.hm = tab + 2 * n;
+        p.ckp = ck;
+        p.ckm = ck + n;
+        p.circ = circ ? 1 : 0;
+        p.job[0].src = f;
+        p.job[0].tgt[0] = out;
+        p.job[0].kind = acc ? JOB_SINGLE : JOB_STORE;
+        p.job[0].coef[0] = acc;
+        p.job[0].sign = shift;
+        e = launch_pass(p, st);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(tab);
+    return e != cudaSuccess ? e : e2;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1279,46 +1330,37 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
     cudaGetLastError();
     int rc = ensure_prepared();
     if (rc != ES_OK) return rc;
-    const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
-    const bool circ = !fft_axis(n, nx);
-    std::vector<float2> tw, hp, hm;
-    std::vector<double> ckp64, ckm64;
-    axis_tables(n, d, tw, hp, hm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
-    std::vector<float> ckp(ckp64.begin(), ckp64.end()), ckm(ckm64.begin(), ckm64.end());
-    float2* tab = nullptr;
-    CK(cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4));
-    float* ck = reinterpret_cast<float*>(tab + 3 * n);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpy(tab, tw.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(tab + n, hp.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(tab + 2 * n, hm.data(), n * 8, cudaMemcpyHostToDevice);
-    if (circ && e == cudaSuccess) e = cudaMemcpy(ck, ckp.data(), n * 4, cudaMemcpyHostToDevice);
-    if (circ && e == cudaSuccess) e = cudaMemcpy(ck + n, ckm.data(), n * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        PassParams p;
-        std::memset(&p, 0, sizeof p);
-        p.nx = nx;
-        p.ny = ny;
-        p.nz = nz;
-        p.axis = axis;
-        p.n = n;
-        p.njobs = 1;
-        p.nsim = 1;
-        p.tw = tab;
-        p.hp = tab + n;
-        p.hm = tab + 2 * n;
-        p.ckp = ck;
-        p.ckm = ck + n;
-        p.circ = circ ? 1 : 0;
-        p.job[0].src = f;
-        p.job[0].tgt[0] = out;
-        p.job[0].kind = JOB_STORE;
-        p.job[0].sign = shift;
-        e = launch_pass(p, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
-    cudaFree(tab);
+    cudaError_t e = derivative_pass(f, nx, ny, nz, axis, d, shift, out, nullptr, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "es_derivative");
+    return ES_OK;
+}
+
+int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, double dz, float* out, void* stream)
+{
+    if (!f || !out || f == out || !(dx > 0) || !(dy > 0) || !(dz > 0)) return ES_ERR_ARG;
+    if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return ES_ERR_SIZE;
+    if (!is_device_ptr(f) || !is_device_ptr(out)) return ES_ERR_ARG;
+    cudaGetLastError();
+    int rc = ensure_prepared();
+    if (rc != ES_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)nx * ny * nz;
+    float* tmp = nullptr;
+    CK(cudaMalloc(&tmp, 2 * n * sizeof(float)));
+    float* ones = tmp + n;
+    const double d[3] = {dx, dy, dz};
+    cudaError_t e = launch_fill(ones, n, 1.f, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, n * sizeof(float), st);
+    // D(+) D(-) along each axis multiplies bin kappa by -kappa^2 (Nyquist included)
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        e = derivative_pass(f, nx, ny, nz, a, d[a], -1, tmp, nullptr, st);
+        if (e == cudaSuccess) e = derivative_pass(tmp, nx, ny, nz, a, d[a], +1, out, ones, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "es_laplacian");
     return ES_OK;
 }
 

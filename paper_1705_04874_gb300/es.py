@@ -72,6 +72,7 @@ def _load():
                 "es_run_group": ([c_int, ctypes.POINTER(vp), c_int, ctypes.POINTER(c_double), ctypes.POINTER(vp),
                                   pi, ctypes.POINTER(vp)], c_int),
                 "es_derivative": ([vp, c_int, c_int, c_int, c_int, c_double, c_int, vp, vp], c_int),
+                "es_laplacian": ([vp, c_int, c_int, c_int, c_double, c_double, c_double, vp, vp], c_int),
                 "es_last_step_kernel_ms": ([vp, ctypes.POINTER(ctypes.c_float), c_int], c_int),
                 "es_kernels_per_step": ([vp], c_int),
                 "es_model_autotune": ([vp, c_int, ctypes.c_char_p, c_int], c_int),
@@ -94,7 +95,7 @@ def exported_symbols():
     return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream", "es_model_set_precision",
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_smoothed", "es_source_add_force",
             "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
-            "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_last_step_kernel_ms",
+            "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_laplacian", "es_last_step_kernel_ms",
             "es_kernels_per_step", "es_model_autotune", "es_fft_plan",
             "es_fft_plan_select", "es_sur_create", "es_sur_destroy", "es_sur_set_stream", "es_sur_num_params",
             "es_sur_get_params", "es_sur_set_params", "es_sur_set_output_scale", "es_sur_fit_output_scale",
@@ -225,6 +226,18 @@ def es_derivative(f, axis, d, shift, out, stream=None):
     op, ok = _ptr(out, np.float32)
     _check(lib.es_derivative(fp, nx, ny, nz, int(axis), float(d), int(shift), op, _stream_handle(stream)),
            "es_derivative")
+    return out
+
+
+def es_laplacian(f, d, out, stream=None):
+    """out = spectral Laplacian of f (Sec. VI-A, Eq. (8)) for [nz][ny][nx] torch
+    CUDA tensors; d = (dx, dy, dz)."""
+    lib = _load()
+    nz, ny, nx = f.shape
+    fp, fk = _ptr(f, np.float32)
+    op, ok = _ptr(out, np.float32)
+    _check(lib.es_laplacian(fp, nx, ny, nz, float(d[0]), float(d[1]), float(d[2]), op, _stream_handle(stream)),
+           "es_laplacian")
     return out
 
 
