@@ -3,7 +3,7 @@
  * network trained on the solver's own 4C traces that maps a point source's
  * position and moment tensor to its seismograms (the "proxy" for the forward
  * simulation that Das, Chen & Hobson name as future work, Sec. VII-C).  The
- * solver (es.h) stays the fallback and the judge of the surrogate's error.
+ * solver (es.h) stays the fallback and the reference for the surrogate's error.
  *
  * Network (BF16 operands, FP32 accumulation, FP32 master weights, Adam):
  *   x = features(position) = [p, sin(2^j pi p), cos(2^j pi p)], j < nfreq,
