@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the reduced surrogate measurement")
     ap.add_argument("--batched-nt", type=int, default=200, help="time steps of the batched measurement")
     args = ap.parse_args()
     if args.workload == "surrogate":
@@ -331,6 +332,14 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "Mcell-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"3 time steps of the {n}^3 workload ({el:.1f} s)"}
     m.close()
+    if not args.no_surrogate and rank == 0 and world == 1:
+        # the surrogate half of the metric on a reduced catalog (bench.py --workload surrogate
+        # runs the full 682-location, 4092-run one)
+        sur_out, _ = surrogate_pipeline(128, 400, args.sur_lr, args.sur_hidden, args.sur_latent, args.sur_nfreq,
+                                        gemm=False)
+        line["surrogate"] = {"value": sur_out["pipeline_seismograms_per_s"], "unit": "4C seismogram sets/s",
+                             "gate": "relative L2 <= 5 % (held-out, 0.8 margin); served sources checked",
+                             **sur_out}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -591,13 +600,15 @@ def measure_configs(args):
     return 0
 
 
-def measure_surrogate(args):
-    """Surrogate workload: 96^3 marine model, PML 10, 8 x 8 seabed receivers,
-    1024 samples, Ricker 30 Hz; a catalog of 682 Latin-hypercube locations
-    in the reservoir box whose 6 unit-moment responses come from 4092 solver
-    runs; training on the GPU; 10,000 random sources (catalog location,
-    random double couple) served by the surrogate where the gate trusts the
-    location and by the solver elsewhere.  Metric: seismograms/s."""
+def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, gemm=True):
+    """The surrogate workflow on the 96^3 marine model (PML 10, 8 x 8 seabed
+    receivers, 1024 samples, Ricker 30 Hz): a catalog of n_loc Latin-hypercube
+    locations in the reservoir box whose 6 unit-moment responses come from
+    6 n_loc batched solver runs; training on the GPU; the gate; n_src random
+    sources (catalog location, random double couple) served by the surrogate
+    where the gate trusts the location and by the solver elsewhere, each
+    checked against its exact reference.  Returns (summary dict, decoder
+    roofline dict or None)."""
     import torch
     from paper_1705_04874_gb300 import es, surrogate as sur
     torch.cuda.set_device(0)
@@ -606,12 +617,11 @@ def measure_surrogate(args):
     dt = 0.3 * 10.0 / float(cp.max())
     wav = synth.ricker(nt, dt, f0)
     box = synth.reservoir_box((n, n, n), pml)
-    n_loc = args.sur_locations
     locations = synth.latin_hypercube_positions(synth.SplitMix64(4), box, n_loc)
     m = es.Model(rho, cp, cs, dx=10.0, pml=pml)
     rcv = m.seabed_receivers(8, 8)
     out = {"workload": f"96^3 marine, 64 receivers x 1024 samples, {n_loc} catalog locations x 6 unit moment "
-                       f"tensors ({6 * n_loc} solver runs), 10000 served sources"}
+                       f"tensors ({6 * n_loc} solver runs), {n_src} served sources"}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     G = sur.green_catalog(m, locations, nt, dt, rcv, wav, per_batch=16)
@@ -620,11 +630,10 @@ def measure_surrogate(args):
     out["catalog_s"] = round(t_cat, 2)
     solver_rate = 6 * n_loc / t_cat  # seismogram sets per second, batched solver
     pos_n = sur.normalize_positions(locations, box)
-    s = sur.Surrogate(len(rcv), nt, nfreq=args.sur_nfreq, hidden=args.sur_hidden, latent=args.sur_latent,
-                      max_batch=256, seed=1)
+    s = sur.Surrogate(len(rcv), nt, nfreq=nfreq, hidden=hidden, latent=latent, max_batch=256, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = sur.train(s, pos_n, G, epochs=args.sur_epochs, lr=args.sur_lr)
+    hist = sur.train(s, pos_n, G, epochs=epochs, lr=lr)
     torch.cuda.synchronize()
     out["train_s"] = round(time.perf_counter() - t0, 2)
     out["train_loss"] = [float(f"{hist[0]:.3e}"), float(f"{hist[-1]:.3e}")]
@@ -634,7 +643,6 @@ def measure_surrogate(args):
     out["gate_err_median"] = float(f"{np.median(e_loc):.3e}")
     out["gate_err_max"] = float(f"{e_loc.max():.3e}")
     rng = synth.SplitMix64(11)
-    n_src = 10000
     loc = np.minimum(np.floor(rng.uniform(n_src) * n_loc).astype(int), n_loc - 1)
     mts = np.array([synth.random_dc(rng) for _ in range(n_src)])
     # surrogate alone on all sources (rate of the network)
@@ -651,7 +659,7 @@ def measure_surrogate(args):
     sur_rate = n_src / (time.perf_counter() - t0)
     # served pipeline (surrogate where trusted, solver elsewhere) on all the sources, or on
     # the first 1000 when the gate sends more than 2 % of the locations to the solver
-    n_pipe = n_src if trusted.mean() >= 0.98 else 1000
+    n_pipe = n_src if trusted.mean() >= 0.98 else min(n_src, 1000)
     del res
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -669,46 +677,57 @@ def measure_surrogate(args):
         d[b:e] = ((served[b:e] - ref) / sc).reshape(e - b, -1).norm(dim=1) / (ref / sc).reshape(e - b, -1).norm(dim=1)
         del ref
     out["pipeline_sources"] = n_pipe
-    # throughput of the network's GEMMs: tcgen05 (both operands K-major: inference decoder,
-    # dZ), mma.sync (the other storage orders), and the decoder product at the served shape
-    K6 = 6 * args.sur_latent
-    gemm = {"tcgen05_8192": round(gemm_tflops(sur, 8192, 8192, 8192, True), 1),
-            "mma_sync_8192": round(gemm_tflops(sur, 8192, 8192, 8192, False), 1),
-            f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(sur, 256, s.D, K6, True), 1)}
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = float(peaks.get("bf16_tflops", 1900.0))
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    dec = gemm[f"tcgen05_decoder_256x{s.D}x{K6}"]
-    # the decoder product reads its BF16 weights once (N K 2 bytes), the codes (M K 2) and writes
-    # the FP32 output (M N 4): 254 flop/byte at M = 256, below the bf16 ridge (~290), so HBM bounds it
-    dec_flop = 2.0 * 256 * s.D * K6
-    dec_bytes = 2.0 * s.D * K6 + 2.0 * 256 * K6 + 4.0 * 256 * s.D
-    dec_gbs = dec_bytes / (dec_flop / (dec * 1e12)) / 1e9
     out.update({"solver_seismograms_per_s": round(solver_rate, 2), "surrogate_seismograms_per_s": round(sur_rate, 1),
                 "pipeline_seismograms_per_s": round(pipe_rate, 1),
                 "pipeline_solver_fraction": round(float(used_solver.mean()), 4),
                 "served_max_rel_l2": float(f"{float(d.max()):.3e}"),
+                "served_over_5pct": int((d > 0.05).sum()),
                 "speedup_surrogate_vs_solver": round(sur_rate / solver_rate, 1),
                 "speedup_pipeline_vs_solver": round(pipe_rate / solver_rate, 1),
-                "gemm_tflops": gemm,
-                "served_over_5pct": int((d > 0.05).sum()),
-                "network": {"hidden": args.sur_hidden, "latent": args.sur_latent, "nfreq": args.sur_nfreq,
-                            "params": s.num_params(), "epochs": args.sur_epochs, "lr": args.sur_lr}})
+                "network": {"hidden": hidden, "latent": latent, "nfreq": nfreq, "params": s.num_params(),
+                            "epochs": epochs, "lr": lr}})
+    roof = None
+    if gemm:
+        # throughput of the network's GEMMs: tcgen05 (both operands K-major: inference decoder,
+        # dZ), mma.sync (the other storage orders), and the decoder product at the served shape
+        K6 = 6 * latent
+        g = {"tcgen05_8192": round(gemm_tflops(sur, 8192, 8192, 8192, True), 1),
+             "mma_sync_8192": round(gemm_tflops(sur, 8192, 8192, 8192, False), 1),
+             f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(sur, 256, s.D, K6, True), 1)}
+        out["gemm_tflops"] = g
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        dec = g[f"tcgen05_decoder_256x{s.D}x{K6}"]
+        # the decoder product reads its BF16 weights once (N K 2 bytes), the codes (M K 2) and writes
+        # the FP32 output (M N 4): 254 flop/byte at M = 256, below the bf16 ridge (~290), so HBM bounds it
+        dec_flop = 2.0 * 256 * s.D * K6
+        dec_bytes = 2.0 * s.D * K6 + 2.0 * 256 * K6 + 4.0 * 256 * s.D
+        dec_gbs = dec_bytes / (dec_flop / (dec * 1e12)) / 1e9
+        roof = {"bound": "hbm", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
+                "achieved": round(dec_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(dec_gbs / hbm, 4),
+                "traffic": None, "algorithmic_bytes": dec_bytes, "tflops": dec, "tensor_peak": peak,
+                "tensor_frac": round(dec / peak, 4), "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     s.close()
     m.close()
+    del G
+    torch.cuda.empty_cache()
+    return out, roof
+
+
+def measure_surrogate(args):
+    """Surrogate workload (C5): 682 catalog locations x 6 unit moment tensors
+    (4092 solver runs), training, gate, 10,000 served sources.  Metric:
+    seismograms/s of the served pipeline."""
+    out, roof = surrogate_pipeline(args.sur_locations, args.sur_epochs, args.sur_lr, args.sur_hidden,
+                                   args.sur_latent, args.sur_nfreq)
     print(json.dumps({"metric": "seismograms/s", "value": out["pipeline_seismograms_per_s"],
                       "unit": "4C seismogram sets/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16/f32",
-                      "data": "synthetic", "config": {"workload": out["workload"]},
-                      "roofline": {"bound": "hbm", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
-                                   "achieved": round(dec_gbs, 1), "peak": hbm, "unit": "GB/s",
-                                   "frac": round(dec_gbs / hbm, 4), "traffic": None,
-                                   "algorithmic_bytes": dec_bytes, "tflops": dec, "tensor_peak": peak,
-                                   "tensor_frac": round(dec / peak, 4),
-                                   "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+                      "data": "synthetic", "config": {"workload": out["workload"]}, "roofline": roof,
                       "surrogate": out}))
     return 0
 
