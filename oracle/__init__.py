@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("pml", ctypes.c_int), ("pml_alpha0", ctypes.c_double),
                 ("pml_cref", ctypes.c_double), ("dt", ctypes.c_double), ("nt", ctypes.c_int),
-                ("deriv_mode", ctypes.c_int), ("nthreads", ctypes.c_int)]
+                ("deriv_mode", ctypes.c_int), ("nthreads", ctypes.c_int), ("tau", ctypes.c_double)]
 
 
 class Source(ctypes.Structure):
@@ -167,10 +167,14 @@ def pml_profile(n, L, alpha0, cref, d, dt, stag):
 
 def simulate(rho, cp, cs, *, dx, dy=None, dz=None, dt, nt, pml=10, pml_alpha0=2.0,
              pml_cref=0.0, sources=(), receivers=None, state=None, energy=False,
-             deriv_mode=0, nthreads=0):
+             deriv_mode=0, nthreads=0, tau=0.0):
     """Run nt leapfrog steps (Sec. II-A) and return a dict with 'traces'
     [4][n_rcv][nt] (p, vx, vy, vz), optionally 'state' [9][nz][ny][nx] (final
-    totals vx vy vz sxx syy szz sxy sxz syz) and 'energy' [nt].
+    totals vx vy vz sxx syy szz sxy sxz syz) and 'energy' [nt].  tau > 0 adds
+    the Kelvin-Voigt terms of Eq. (1)-(2) with chi = tau lambda, eta = tau mu,
+    the time derivative of the strain rate taken as the backward difference
+    of the velocity derivatives over one step (v^{n-1/2} of the given state
+    counts as the previous velocity at the first step).
 
     sources: iterable of dicts {kind: 'moment'|'force', pos: (ix,iy,iz),
     m: 6 moment components (xx yy zz xy xz yz) or 3 force components,
@@ -182,7 +186,7 @@ def simulate(rho, cp, cs, *, dx, dy=None, dz=None, dt, nt, pml=10, pml_alpha0=2.
     dz = dx if dz is None else dz
     p = Params(nx, ny, nz, float(dx), float(dy), float(dz), int(pml), float(pml_alpha0),
                float(pml_cref), float(dt), int(nt), int(deriv_mode),
-               int(nthreads or default_threads()))
+               int(nthreads or default_threads()), float(tau))
     srcs = list(sources)
     arr = (Source * max(1, len(srcs)))()
     keep = []

@@ -360,6 +360,7 @@ typedef struct {
     int nt;
     int deriv_mode;   /* 0: 1D FFT, 1: naive DFT, 2: 3D FFT */
     int nthreads;
+    double tau;       /* Kelvin-Voigt relaxation time (chi = tau lambda, eta = tau mu); 0 = elastic */
 } orc_params;
 
 typedef struct {
@@ -486,7 +487,9 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
     double *tot[NF], *D = malloc(sizeof(double) * ncell);
     for (int f = 0; f < NF; ++f) tot[f] = malloc(sizeof(double) * ncell);
     double *vold[3] = {NULL, NULL, NULL};
-    if (energy_out) for (int c = 0; c < 3; ++c) vold[c] = malloc(sizeof(double) * ncell);
+    const double tau = p->tau > 0 ? p->tau : 0.0;
+    double *D2 = tau > 0 ? malloc(sizeof(double) * ncell) : NULL;
+    if (energy_out || tau > 0) for (int c = 0; c < 3; ++c) vold[c] = malloc(sizeof(double) * ncell);
 
 #define TOTAL(f) do { OMP_TOTAL for (size_t q = 0; q < ncell; ++q) { double s_ = 0.0; \
         for (int a_ = 0; a_ < 3; ++a_) if (split[f][a_]) s_ += split[f][a_][q]; tot[f][q] = s_; } } while (0)
@@ -494,7 +497,9 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
     for (int n = 0; n < nt; ++n) {
         /* ---- velocity half: v^{n-1/2} -> v^{n+1/2} from sigma^n ---- */
         for (int f = SXX; f <= SYZ; ++f) TOTAL(f);
-        if (energy_out) for (int c = 0; c < 3; ++c) { TOTAL(VX + c); memcpy(vold[c], tot[VX + c], sizeof(double) * ncell); }
+        /* v^{n-1/2}: the energy's old velocity and the viscous terms' backward difference */
+        if (energy_out || tau > 0)
+            for (int c = 0; c < 3; ++c) { TOTAL(VX + c); memcpy(vold[c], tot[VX + c], sizeof(double) * ncell); }
         for (int t = 0; t < 9; ++t) {
             const term *T = &VEL_TERMS[t];
             orc_deriv(tot[T->source], nx, ny, nz, T->axis, dxyz[T->axis], T->shift, D, p->deriv_mode, p->nthreads);
@@ -524,8 +529,11 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
         /* ---- stress half: sigma^n -> sigma^{n+1} from v^{n+1/2} ---- */
         for (int f = VX; f <= VZ; ++f) TOTAL(f);
         for (int a = 0; a < 3; ++a) {
-            /* normal stresses: d sigma_ii^(a) = dt (lambda + 2 mu delta_ia) dv_a/dx_a */
+            /* normal stresses: d sigma_ii^(a) = dt (lambda + 2 mu delta_ia) dv_a/dx_a
+             * + (chi + 2 eta delta_ia) (dv_a/dx_a at n+1/2 minus at n-1/2), Eq. (2) with the
+             * time derivative of the strain rate as a backward difference over one step */
             orc_deriv(tot[VX + a], nx, ny, nz, a, dxyz[a], -1, D, p->deriv_mode, p->nthreads);
+            if (tau > 0) orc_deriv(vold[a], nx, ny, nz, a, dxyz[a], -1, D2, p->deriv_mode, p->nthreads);
             for (int t = 0; t < 9; ++t) {
                 const term *T = &STR_TERMS[t];
                 if (T->axis != a) continue;
@@ -535,19 +543,26 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
                     size_t q = IDX(i, j, k);
                     int ia = a == 0 ? i : (a == 1 ? j : k);
                     double c = lam[q] + (diag ? 2.0 * mu[q] : 0.0);
-                    s[q] = Pc[a][ia] * (Pc[a][ia] * s[q] + dt * c * D[q]);
+                    double inc = dt * c * D[q];
+                    if (tau > 0) inc += tau * c * (D[q] - D2[q]);
+                    s[q] = Pc[a][ia] * (Pc[a][ia] * s[q] + inc);
                 }
             }
         }
         for (int t = 0; t < 6; ++t) {
             const term *T = &SHEAR_TERMS[t];
             orc_deriv(tot[T->source], nx, ny, nz, T->axis, dxyz[T->axis], T->shift, D, p->deriv_mode, p->nthreads);
+            if (tau > 0)
+                orc_deriv(vold[T->source - VX], nx, ny, nz, T->axis, dxyz[T->axis], T->shift, D2, p->deriv_mode,
+                          p->nthreads);
             double *s = split[T->target][T->axis];
             const double *coef = mue[T->target - SXY];
             OMP_CELLS for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
                 size_t q = IDX(i, j, k);
                 int ia = T->axis == 0 ? i : (T->axis == 1 ? j : k);
-                s[q] = Ps[T->axis][ia] * (Ps[T->axis][ia] * s[q] + dt * coef[q] * D[q]);
+                double inc = dt * coef[q] * D[q];
+                if (tau > 0) inc += tau * coef[q] * (D[q] - D2[q]);
+                s[q] = Ps[T->axis][ia] * (Ps[T->axis][ia] * s[q] + inc);
             }
         }
         for (int e = 0; e < nsrc; ++e) {          /* R-src, moment tensor */
@@ -588,7 +603,7 @@ int orc_simulate(const orc_params *p, const double *rho, const double *cp, const
     for (int f = 0; f < NF; ++f) { free(tot[f]); for (int a = 0; a < 3; ++a) free(split[f][a]); }
     for (int c = 0; c < 3; ++c) { free(b[c]); free(mue[c]); free(vold[c]); }
     for (int a = 0; a < 3; ++a) { free(Pc[a]); free(Ps[a]); }
-    free(lam); free(mu); free(D);
+    free(lam); free(mu); free(D); free(D2);
     return 0;
 }
 
