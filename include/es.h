@@ -74,6 +74,21 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
 #define ES_PREC_COMPENSATED 1
 int es_model_set_precision(es_model* m, int mode);
 
+/* Kelvin-Voigt viscosity (Eq. (1)-(2): the chi and eta terms, zero in the
+ * paper's own runs), read as chi = tau lambda and eta = tau mu with one
+ * relaxation time tau [s] >= 0, and the time derivative of the strain rate as
+ * the backward difference of the velocity derivatives over one step:
+ *   sigma^{n+1} = sigma^n + C D(dt v^{n+1/2} + tau (v^{n+1/2} - v^{n-1/2}))
+ * (C the elastic stiffness of each term, split-field PML as usual).  tau = 0
+ * is the elastic scheme.  For one Fourier mode the amplification z solves
+ * z^2 + (q (1 + r) - 2) z + 1 - q r = 0, q = (c dt |kappa|)^2, r = tau / dt:
+ * es_run returns ES_ERR_UNSTABLE unless q_max (1 + 2 tau / dt) <= 4.  The
+ * first viscous run allocates 6 floats per cell and simulation and starts
+ * from v^{n-1/2} = the current velocity; es_state_reset zeroes it and
+ * es_state_set sets it to the given velocity.  Adds one kernel per step
+ * (after the velocity half, before the stress passes). */
+int es_model_set_viscosity(es_model* m, double tau);
+
 /* Anisotropic spacing [m] (the paper's grid is 12.5 / 12.5 / 10 m, Sec. II-B). */
 int es_model_set_spacing(es_model* m, double dx, double dy, double dz);
 
@@ -248,7 +263,8 @@ int es_fft_plan_select(int pass_kind, int n, int ra, int rb);
 
 /* Device time [ms] of each kernel of the last time step of the last es_run
  * (CUDA events around each kernel launch of that step), in launch order:
- * vel-x, vel-y, vel-z, str-x, str-y, str-z, inject, record.  n = capacity;
+ * vel-x, vel-y, vel-z, [force inject], [viscous combine], str-x, str-y,
+ * str-z, inject, record (bracketed ones only when present).  n = capacity;
  * returns the number written (>= 0) or a negative status. */
 int es_last_step_kernel_ms(es_model* m, float* ms, int n);
 

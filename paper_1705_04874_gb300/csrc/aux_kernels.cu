@@ -72,6 +72,28 @@ cudaError_t launch_inject(float* const* fields, long long fstride, const SourceD
     return cudaGetLastError();
 }
 
+// Kelvin-Voigt source of the stress passes: w = a v - b vold, vold <- v, for
+// the three velocity components ([c][sim][cell], n = cells x simulations each)
+__global__ void visc_combine_kernel(float* const* fields, float* vold, float* w, size_t n, float a, float b)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = fields[VX + c][i];
+            w[c * n + i] = a * v - b * vold[c * n + i];
+            vold[c * n + i] = v;
+        }
+}
+
+cudaError_t launch_visc_combine(float* const* fields, float* vold, float* w, size_t n, float a, float b,
+                                cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
+    visc_combine_kernel<<<(unsigned)blocks, 256, 0, st>>>(fields, vold, w, n, a, b);
+    return cudaGetLastError();
+}
+
 __global__ void fill_kernel(float* p, size_t n, float v)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;

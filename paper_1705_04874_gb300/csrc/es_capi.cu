@@ -219,7 +219,7 @@ struct Src {
     int nw;
 };
 
-const int KPS_MAX = 9;  // kernels per step (8, +1 with force sources)
+const int KPS_MAX = 10;  // kernels per step (8, +1 with force sources, +1 with viscosity)
 
 }  // namespace
 
@@ -243,6 +243,14 @@ struct es_model {
     float *ckp[3] = {}, *ckm[3] = {};  // circulant kernels (axes without an FFT pass)
     float *ckp_lo[3] = {}, *ckm_lo[3] = {};  // their low parts (compensated mode)
     int prec = ES_PREC_FP32;
+    // Kelvin-Voigt viscosity (chi = tau lambda, eta = tau mu): v^{n-1/2} kept per velocity
+    // component and the stress passes' combined source w = (dt + tau) v^{n+1/2} - tau v^{n-1/2},
+    // [3][sim][cell] each, allocated with the first viscous run
+    double tau = 0.0;
+    char* vpool = nullptr;
+    int vpool_nsim = 0;
+    float* vold = nullptr;
+    float* wv = nullptr;
     float *pc[3] = {}, *ps[3] = {};
     int* d_int = nullptr;  // [0] step counter, [1] current step, [2] non-finite flag
     std::vector<Src> srcs;
@@ -450,9 +458,26 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         mark(false);
         ++k;
     }
+    const bool visc = m->tau > 0.0;
+    const size_t nv = m->ncell * (size_t)m->nsim;
+    if (visc) {
+        // w = (dt + tau) v^{n+1/2} - tau v^{n-1/2}, then v^{n-1/2} <- v^{n+1/2}: the stress passes
+        // take c D(w) = dt c D(v) + tau c (D(v^{n+1/2}) - D(v^{n-1/2})) (Eq. (2), chi = tau lambda,
+        // eta = tau mu, backward difference of the strain rate)
+        mark(true);
+        CK(launch_visc_combine(m->d_fields, m->vold, m->wv, nv, (float)((double)dt + m->tau), (float)m->tau, st));
+        mark(false);
+        ++k;
+    }
     for (int a = 0; a < 3; ++a) {
         PassParams p = make_pass(m, a, true, dt);
         p.pdl = a == 0 ? 2 : 1;
+        if (visc) {
+            p.dt = 1.f;
+            for (int j = 0; j < p.njobs; ++j)
+                for (int c = 0; c < 3; ++c)
+                    if (p.job[j].src == m->f[VX + c]) p.job[j].src = m->wv + (size_t)c * nv;
+        }
         mark(true);
         CK(launch_pass(p, st));
         mark(false);
@@ -609,6 +634,7 @@ const char* es_last_error(void) { return g_err; }
 void es_model_destroy(es_model* m)
 {
     if (!m) return;
+    cudaFree(m->vpool);
     for (auto& s : m->srcs) cudaFree(s.d_w);
     cudaFree(m->d_src);
     cudaFree(m->d_rec);
@@ -752,6 +778,13 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         return rc;
     }
     *out = m;
+    return ES_OK;
+}
+
+int es_model_set_viscosity(es_model* m, double tau)
+{
+    if (!m || !(tau >= 0.0) || !std::isfinite(tau)) return ES_ERR_ARG;
+    m->tau = tau;
     return ES_OK;
 }
 
@@ -908,6 +941,7 @@ int es_state_reset(es_model* m)
         for (int f = 0; f < NFIELD; ++f)
             if (m->slab[a][f]) CK(cudaMemsetAsync(m->slab[a][f], 0, slab_count(m, a) * 4 * ns, m->stream));
     CK(cudaMemsetAsync(m->d_int, 0, 16, m->stream));
+    if (m->vpool) CK(cudaMemsetAsync(m->vpool, 0, 6 * m->ncell * (size_t)m->vpool_nsim * sizeof(float), m->stream));
     CK(cudaStreamSynchronize(m->stream));
     m->steps_done = 0;
     return ES_OK;
@@ -941,6 +975,13 @@ int es_state_set(es_model* m, const float* fields)
                                     m->nz, m->L, a == first, m->stream));
             }
     }
+    // viscous runs: the given velocity also stands for v^{n-1/2} (no strain-rate history)
+    if (m->vpool && m->vpool_nsim == m->nsim) {
+        const size_t nv = m->ncell * (size_t)m->nsim;
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpyAsync(m->vold + c * nv, m->f[VX + c], nv * sizeof(float), cudaMemcpyDeviceToDevice,
+                               m->stream));
+    }
     CK(cudaStreamSynchronize(m->stream));
     return ES_OK;
 }
@@ -955,9 +996,25 @@ static int run_prepare(es_model* m, int nt, double* pdt, const int* rcv, int n_r
     cudaGetLastError();  // launch checks below must not see an earlier, unrelated error
     if (n_rcv > 0 && (!rcv || !traces)) return ES_ERR_ARG;
     if (!(dt > 0)) es_model_default_dt(m, &dt);
-    // stability of the staggered pseudo-spectral leapfrog: c dt |kappa_max| <= 2
+    // stability of the staggered pseudo-spectral leapfrog: c dt |kappa_max| <= 2; with the
+    // viscous terms every mode needs q (1 + 2 tau / dt) <= 4, q = (c dt |kappa_max|)^2
     const double s = std::sqrt(1.0 / (m->d[0] * m->d[0]) + 1.0 / (m->d[1] * m->d[1]) + 1.0 / (m->d[2] * m->d[2]));
-    if ((double)m->cp_max * dt * s > 2.0 / 3.14159265358979323846) return ES_ERR_UNSTABLE;
+    const double qmax = std::pow((double)m->cp_max * dt * 3.14159265358979323846 * s, 2.0);
+    if (qmax * (1.0 + 2.0 * m->tau / dt) > 4.0) return ES_ERR_UNSTABLE;
+    if (m->tau > 0.0 && (!m->vpool || m->vpool_nsim != m->nsim)) {
+        // first viscous run at this batch size: v^{n-1/2} starts as the current velocity
+        const size_t nv = m->ncell * (size_t)m->nsim;
+        char* pool = nullptr;
+        CK(cudaMalloc(&pool, 6 * nv * sizeof(float)));
+        cudaFree(m->vpool);
+        m->vpool = pool;
+        m->vpool_nsim = m->nsim;
+        m->vold = reinterpret_cast<float*>(pool);
+        m->wv = m->vold + 3 * nv;
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpyAsync(m->vold + c * nv, m->f[VX + c], nv * sizeof(float), cudaMemcpyDeviceToDevice,
+                               m->stream));
+    }
 
     std::vector<int> h_rcv;
     if ((rc = fetch(rcv, (size_t)n_rcv * 3, h_rcv, m->stream)) != ES_OK) return rc;
@@ -1248,7 +1305,7 @@ int es_kernels_per_step(const es_model* m)
 {
     if (!m) return ES_ERR_ARG;
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
-    return 8 + (has_force ? 1 : 0);
+    return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0);
 }
 
 int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv)

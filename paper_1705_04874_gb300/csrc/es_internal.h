@@ -95,6 +95,8 @@ cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, 
                              const float* ev_amp, const int* ev_shift, int n_events, int n_out,
                              float* gather, cudaStream_t st);
 cudaError_t launch_fill(float* p, size_t n, float v, cudaStream_t st);
+cudaError_t launch_visc_combine(float* const* fields, float* vold, float* w, size_t n, float a, float b,
+                                cudaStream_t st);
 cudaError_t launch_nonfinite(float* const* fields, size_t n, int* flag, cudaStream_t st);
 cudaError_t launch_fill_slab(const float* total, float* slab, int axis, int nx, int ny, int nz,
                              int L, int copy, cudaStream_t st);

@@ -54,6 +54,7 @@ def _load():
                 "es_model_set_pml": ([vp, c_double, c_double], c_int),
                 "es_model_set_stream": ([vp, vp], c_int),
                 "es_model_set_precision": ([vp, c_int], c_int),
+                "es_model_set_viscosity": ([vp, c_double], c_int),
                 "es_model_default_dt": ([vp, ctypes.POINTER(c_double)], c_int),
                 "es_source_set": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
                 "es_source_add": ([vp, pi, ctypes.POINTER(c_double), vp, c_int], c_int),
@@ -92,7 +93,7 @@ def _load():
 
 def exported_symbols():
     """Names the binding expects the library to export."""
-    return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream", "es_model_set_precision",
+    return ["es_model_create", "es_model_set_spacing", "es_model_set_pml", "es_model_set_stream", "es_model_set_precision", "es_model_set_viscosity",
             "es_model_default_dt", "es_source_set", "es_source_add", "es_source_add_smoothed", "es_source_add_force",
             "es_source_clear", "es_batch_set", "es_state_reset", "es_state_get", "es_state_set", "es_run",
             "es_run_group", "es_superpose", "es_superpose_noalloc", "es_seabed_receivers", "es_derivative", "es_laplacian", "es_last_step_kernel_ms",
@@ -279,6 +280,10 @@ class Model:
 
     def set_spacing(self, dx, dy, dz):
         _check(self._lib.es_model_set_spacing(self._h, dx, dy, dz), "es_model_set_spacing")
+
+    def set_viscosity(self, tau):
+        """Kelvin-Voigt relaxation time tau [s] (chi = tau lambda, eta = tau mu): es_model_set_viscosity."""
+        _check(self._lib.es_model_set_viscosity(self._h, float(tau)), "es_model_set_viscosity")
 
     def set_precision(self, mode):
         """ES_PREC_FP32 (0) or ES_PREC_COMPENSATED (1): es_model_set_precision."""
