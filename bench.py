@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm", "serve"])
+    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm", "serve", "paper"])
     ap.add_argument("--gemm-small", action="store_true", help="gemm workload: the decoder shape only")
     ap.add_argument("--sur-locations", type=int, default=682)
     ap.add_argument("--sur-epochs", type=int, default=150)
@@ -217,6 +217,8 @@ def main():
         return measure_gemm(args)
     if args.workload == "serve":
         return measure_serve(args)
+    if args.workload == "paper":
+        return measure_paper(args)
     w = workload(args.workload)
     if args.nt:
         w["nt"] = args.nt
@@ -482,6 +484,52 @@ def measure_serve(args):
     print(json.dumps({"metric": "seismograms/s", "value": round(n_src / (ms * 1e-3), 1),
                       "unit": "4C seismogram sets/s (network only)", "ms_per_10k": round(ms, 2),
                       "batches": n_batches, "dtype": "bf16/f32", "data": "synthetic"}))
+    return 0
+
+
+def measure_paper(args):
+    """The paper's own workload shape: 125 x 75 x 301 cells (12.5 / 12.5 / 10 m), PML 10, a double
+    couple in the reservoir box, Ricker 30 Hz, 2000 steps (--nt overrides), 105 x 55 seabed receivers
+    (every interior x-y point).  No axis length has an FFT plan, so every pass is a circulant pass.
+    Device time of whole es_run calls, --steps timed after --warmup."""
+    import torch
+    from paper_1705_04874_gb300 import es
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    shape, d, pml = (301, 75, 125), (12.5, 12.5, 10.0), 10
+    nt = args.nt or 2000
+    rho, cp, cs = synth.marine_model(shape=shape, seed=1)
+    dt = 0.3 * min(d) / float(cp.max())
+    box = synth.reservoir_box(shape, pml)
+    pos = tuple((lo + hi) // 2 for lo, hi in box)
+    with es.Model(rho, cp, cs, dx=d[0], pml=pml, stream=stream) as m:
+        m.set_spacing(*d)
+        rcv = torch.from_numpy(m.seabed_receivers(105, 55)).cuda()
+        m.source_set(pos, synth.double_couple_sdr(30, 60, 90), torch.from_numpy(synth.ricker(nt, dt, 30.0)).cuda())
+        tr = torch.empty((4, rcv.shape[0], nt), device="cuda")
+
+        def run():
+            m.state_reset()
+            m.run(nt, dt, rcv, tr)
+        for _ in range(max(args.warmup, 0)):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        kern = m.last_step_kernel_ms()
+    cells = 125 * 75 * 301
+    print(json.dumps({"metric": "Mcell-steps/s", "value": round(cells * nt / (ms * 1e-3) / 1e6, 1),
+                      "unit": "Mcell-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(ms, 3), "s_per_source": round(ms * 1e-3, 3), "dtype": "f32",
+                      "data": "synthetic",
+                      "config": {"workload": "the paper's grid 125x75x301, 12.5/12.5/10 m, PML 10, "
+                                             f"{nt} steps, 105x55 seabed receivers, circulant passes"},
+                      "kernels_ms": [round(float(k), 4) for k in kern]}))
     return 0
 
 

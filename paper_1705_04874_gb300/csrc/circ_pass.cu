@@ -45,11 +45,13 @@ __host__ __device__ inline int circ_pad(int n) { return (n + OB - 1) / OB * OB; 
 // multiple of 4, so the window loads are aligned float4s
 __host__ __device__ inline int circ_koff(int n) { return KOFF + (((JB - 1 - KOFF - n) % 4) + 4) % 4; }
 
-// shared floats: input and output tiles [pad(n)][ROW] + kernel row [2 pad(n) + 2 KOFF + OB + 8]
+// shared floats: the input tile [pad(n)][ROW] (the x pass also an output tile
+// of that shape) + the kernel row [2 pad(n) + 2 KOFF + OB + 8] (high and low
+// parts in the compensated mode)
 __host__ __device__ inline int circ_row_len(int n) { return 2 * circ_pad(n) + 2 * KOFF + OB + 8; }
-__host__ __device__ inline size_t circ_smem(int n, bool comp)
+__host__ __device__ inline size_t circ_smem(int n, bool comp, bool two_tiles)
 {
-    return sizeof(float) * (2 * (size_t)circ_pad(n) * ROW + (comp ? 2 : 1) * (size_t)circ_row_len(n));
+    return sizeof(float) * ((two_tiles ? 2 : 1) * (size_t)circ_pad(n) * ROW + (comp ? 2 : 1) * (size_t)circ_row_len(n));
 }
 
 // scalar epilogue for one cell (same arithmetic as epilogue_pair)
@@ -91,8 +93,8 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
 // KOFF - (OB - 1) + 1 > 0 since pad(n) - n < OB, a multiple of 4, and its
 // OBV + JB entries end at or below koff + n + pad(n) + OB, inside the row
 // (circ_row_len).  COMP: cl is the low part of the row (same layout).
-template <bool COMP, int OBV>
-__device__ __forceinline__ void circ_convolve(const float* tile, float* out, const float* cw, const float* cl, int n,
+template <bool COMP, int OBV, class Emit>
+__device__ __forceinline__ void circ_convolve(const float* tile, Emit emit, const float* cw, const float* cl, int n,
                                               int warp, int lane)
 {
     constexpr int W = OBV + JB;  // window length, a multiple of 4
@@ -146,9 +148,8 @@ __device__ __forceinline__ void circ_convolve(const float* tile, float* out, con
         }
 #pragma unroll
         for (int t = 0; t < OBV; ++t)
-            if (i0 + t < n) out[(i0 + t) * ROW + lane] = COMP ? __fadd_rn(acc[t], lo[t]) : acc[t];
+            if (i0 + t < n) emit(i0 + t, COMP ? __fadd_rn(acc[t], lo[t]) : acc[t]);
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n, int tid)
@@ -161,15 +162,21 @@ __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n
     }
 }
 
+// Long axes (n >= CIRC_DIRECT_N) give every warp several 16-output chunks: the y and z
+// passes then run the epilogue straight from the registers (no output tile, half the
+// shared memory, twice the resident CTAs); shorter axes keep the output tile so that all
+// eight warps share the epilogue.
+constexpr int CIRC_DIRECT_N = 192;
+
 // y and z passes: blockIdx.x = (tile of 32 consecutive x) x outer x simulation, blockIdx.y = job
-template <bool COMP>
+template <bool COMP, bool DIRECT>
 __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constant__ PassParams p)
 {
     extern __shared__ float csm[];
     const int n = p.n, np = circ_pad(n);
     float* tile = csm;
-    float* out = tile + (size_t)np * ROW;
-    float* cw = out + (size_t)np * ROW;
+    float* out = tile + (size_t)np * ROW;  // used only without DIRECT
+    float* cw = out + (DIRECT ? 0 : (size_t)np * ROW);
     float* cl = cw + circ_row_len(n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const PassJob& J = p.job[blockIdx.y];
@@ -195,14 +202,31 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
         tile[pos * ROW + c] = v;
     }
     __syncthreads();
-    circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
-    if (p.pdl == 1) pdl_wait();
-    for (int it = tid; it < n * TP; it += CTHREADS) {
-        const int pos = it / TP, c = it % TP;
-        const int x = x0 + c;
-        if (x >= p.nx) continue;
-        const int y = p.axis == 1 ? pos : outer, z = p.axis == 1 ? outer : pos;
-        epilogue_one(p, J, base0 + c + (size_t)pos * est, pos, x, y, z, out[pos * ROW + c], off, soff);
+    if constexpr (DIRECT) {
+        if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
+        // lane = x column: the warp's outputs of one position are 32 consecutive cells, so the
+        // epilogue runs straight from the registers, coalesced
+        const int x = x0 + lane;
+        circ_convolve<COMP, COMP ? 8 : OB>(
+            tile,
+            [&](int pos, float d) {
+                if (x >= p.nx) return;
+                const int y = p.axis == 1 ? pos : outer, z = p.axis == 1 ? outer : pos;
+                epilogue_one(p, J, base0 + lane + (size_t)pos * est, pos, x, y, z, d, off, soff);
+            },
+            cw, cl, n, warp, lane);
+    } else {
+        circ_convolve<COMP, COMP ? 8 : OB>(
+            tile, [&](int pos, float d) { out[pos * ROW + lane] = d; }, cw, cl, n, warp, lane);
+        __syncthreads();
+        if (p.pdl == 1) pdl_wait();
+        for (int it = tid; it < n * TP; it += CTHREADS) {
+            const int pos = it / TP, c = it % TP;
+            const int x = x0 + c;
+            if (x >= p.nx) continue;
+            const int y = p.axis == 1 ? pos : outer, z = p.axis == 1 ? outer : pos;
+            epilogue_one(p, J, base0 + c + (size_t)pos * est, pos, x, y, z, out[pos * ROW + c], off, soff);
+        }
     }
 }
 
@@ -235,7 +259,9 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
         tile[pos * ROW + r] = __ldg(src + e);
     }
     __syncthreads();
-    circ_convolve<COMP, COMP ? 8 : OB>(tile, out, cw, cl, n, warp, lane);
+    circ_convolve<COMP, COMP ? 8 : OB>(
+        tile, [&](int pos, float d) { out[pos * ROW + lane] = d; }, cw, cl, n, warp, lane);
+    __syncthreads();
     if (p.pdl == 1) pdl_wait();
     for (int e = tid; e < nl * n; e += CTHREADS) {
         const int r = e / n, pos = e % n;
@@ -247,15 +273,21 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
 
 }  // namespace
 
-size_t circ_smem_bytes(int n) { return circ_smem(n, false); }
+size_t circ_smem_bytes(int n) { return circ_smem(n, false, true); }
 
 cudaError_t prepare_circ_kernels()
 {
-    const int maxb = (int)circ_smem(CIRC_MAX_N, true);
-    cudaError_t e = cudaFuncSetAttribute(circ_strided<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_strided<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(circ_x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    const int maxb = (int)circ_smem(CIRC_MAX_N, true, true);
+    cudaError_t e = cudaSuccess;
+    auto opt = [&](auto kernel) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    };
+    opt(circ_x<false>);
+    opt(circ_x<true>);
+    opt(circ_strided<false, false>);
+    opt(circ_strided<false, true>);
+    opt(circ_strided<true, false>);
+    opt(circ_strided<true, true>);
     return e;
 }
 
@@ -263,16 +295,22 @@ cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
 {
     if (p.n < 2 || p.n > CIRC_MAX_N || !p.ckp || !p.ckm) return cudaErrorInvalidValue;
     if (p.comp && (!p.ckp_lo || !p.ckm_lo)) return cudaErrorInvalidValue;
-    const size_t smem = circ_smem(p.n, p.comp != 0);
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((unsigned)((lines + TP - 1) / TP) * p.nsim, p.njobs);
-        return launch_pass_kernel(p.comp ? circ_x<true> : circ_x<false>, grid, CTHREADS, smem, st, p);
+        return launch_pass_kernel(p.comp ? circ_x<true> : circ_x<false>, grid, CTHREADS,
+                                  circ_smem(p.n, p.comp != 0, true), st, p);
     }
     const int ntx = (p.nx + TP - 1) / TP;
     const int outer = p.axis == 1 ? p.nz : p.ny;
     dim3 grid((unsigned)(ntx * outer) * p.nsim, p.njobs);
-    return launch_pass_kernel(p.comp ? circ_strided<true> : circ_strided<false>, grid, CTHREADS, smem, st, p);
+    const bool direct = p.n >= CIRC_DIRECT_N;
+    const size_t smem = circ_smem(p.n, p.comp != 0, !direct);
+    if (direct)
+        return launch_pass_kernel(p.comp ? circ_strided<true, true> : circ_strided<false, true>, grid, CTHREADS,
+                                  smem, st, p);
+    return launch_pass_kernel(p.comp ? circ_strided<true, false> : circ_strided<false, false>, grid, CTHREADS, smem,
+                              st, p);
 }
 
 }  // namespace es
