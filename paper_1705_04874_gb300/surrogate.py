@@ -152,11 +152,13 @@ class Surrogate:
                                          _dp(g) if grads else None), "es_sur_loss_grad")
         return loss.value, per, g
 
-    def train_step(self, pos, mt, target, lr):
+    def train_step(self, pos, mt, target, lr, want_loss=True):
+        """One Adam step; returns the batch loss, or None with want_loss=False
+        (no device synchronisation: the step stays queued on the stream)."""
         loss = ctypes.c_float()
         _check(self.lib.es_sur_train_step(self._h, _dp(pos), _dp(mt), _dp(target), pos.shape[0], float(lr),
-                                          ctypes.byref(loss)), "es_sur_train_step")
-        return loss.value
+                                          ctypes.byref(loss) if want_loss else None), "es_sur_train_step")
+        return loss.value if want_loss else None
 
 
 # ---------------------------------------------------------------------------
@@ -215,15 +217,11 @@ def combine(G, loc, mt, stream=None):
 def random_moment_tensors(rng, n):
     """Training draws: half random double couples, half general tensors
     (isotropic and CLVD parts included), each of unit norm."""
-    out = np.empty((n, 6))
     u = rng.uniform(n)
-    for i in range(n):
-        if u[i] < 0.5:
-            m = synth.random_dc(rng)
-        else:
-            m = rng.normal(6)
-        out[i] = m / np.sqrt(np.sum(m[:3] ** 2) + 2 * np.sum(m[3:] ** 2))
-    return out
+    dc = synth.random_dc_batch(rng, n)
+    gen = rng.normal(6 * n).reshape(n, 6)
+    out = np.where((u < 0.5)[:, None], dc, gen)
+    return out / np.sqrt(np.sum(out[:, :3] ** 2, axis=1) + 2 * np.sum(out[:, 3:] ** 2, axis=1))[:, None]
 
 
 def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=None, warmup=0.02):
@@ -231,7 +229,7 @@ def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=Non
     location (random_moment_tensors) and regresses the network onto their exact
     seismograms (combine).  pos_n: [n_loc][3] normalized positions.  Learning
     rate: linear warm-up over the first `warmup` fraction of the steps, then a
-    cosine decay."""
+    cosine decay.  Returns the loss of each epoch's last batch."""
     import torch
     n_loc = G.shape[0]
     sur.fit_output_scale(G.view(n_loc * 6, -1))
@@ -248,7 +246,7 @@ def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=Non
         order = order_rng.permutation(N)
         if len(order) % batch:
             order = np.concatenate([order, order[:batch - len(order) % batch]])
-        losses = []
+        loss = None
         for s in range(0, len(order), batch):
             idx = order[s:s + batch]
             tgt = combine(G, loc[idx], mts[idx]).view(len(idx), -1)
@@ -257,9 +255,11 @@ def train(sur, pos_n, G, epochs, lr=2e-3, batch=None, per_loc=8, seed=0, log=Non
             lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / n_steps))
             if step < warmup * n_steps:
                 lr_t *= (step + 1) / (warmup * n_steps)
-            losses.append(sur.train_step(pos_dev[li].contiguous(), mm, tgt, max(lr_t, 1e-6)))
+            last = s + batch >= len(order)
+            # the loss is read back (a synchronisation) once per epoch, on its last batch
+            loss = sur.train_step(pos_dev[li].contiguous(), mm, tgt, max(lr_t, 1e-6), want_loss=last)
             step += 1
-        history.append(float(np.mean(losses)))
+        history.append(float(loss))
         if log and (ep % max(1, epochs // 10) == 0 or ep == epochs - 1):
             log(f"epoch {ep}: loss {history[-1]:.3e}")
     return history
