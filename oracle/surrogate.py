@@ -1,12 +1,14 @@
-"""FP64 oracle of the surrogate network's forward pass, loss and gradients
-(the learned proxy of the forward simulation named as future work in
-Sec. VII-C of the paper; the network itself is this project's design, see
-include/es_surrogate.h).
+"""FP64 oracle of the surrogate network's forward pass, loss and gradients,
+and of the Adam step that trains it (the learned proxy of the forward
+simulation named as future work in Sec. VII-C of the paper; the network
+itself is this project's design, see include/es_surrogate.h).
 
 TEST INFRASTRUCTURE ONLY (tests and the smoke check).  Plain numpy, float64,
 gradients written out by the chain rule (no autograd), in the same flat
 parameter layout as the CUDA implementation.  Pinned by central finite
-differences in tests/test_oracle_surrogate.py.
+differences, and the Adam step by its closed forms (a constant gradient moves
+every parameter by lr g / (|g| + eps) at every step; a reversed gradient), in
+tests/test_oracle_surrogate.py.
 """
 from __future__ import annotations
 
@@ -92,3 +94,17 @@ def loss_and_grads(params, cfg, pos, mt, target, scale, eps=1e-30):
     for k, (o, s_) in f["lay"].items():
         flat[o:o + int(np.prod(s_))] = g[k].ravel()
     return loss, per_sample, flat
+
+
+def adam_step(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One bias-corrected Adam update, step t >= 1 (Kingma & Ba, "Adam: A
+    Method for Stochastic Optimization", ICLR 2015, Algorithm 1): the first
+    and second moment estimates decay by b1 and b2, are divided by
+    1 - b1^t and 1 - b2^t, and the parameters move by lr * m_hat /
+    (sqrt(v_hat) + eps).  Returns (params, m, v), FP64."""
+    g = np.asarray(grad, np.float64)
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return np.asarray(params, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

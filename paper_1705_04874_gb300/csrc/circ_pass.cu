@@ -12,10 +12,15 @@
 // One CTA: a tile of 32 pencils (32 consecutive x for the y and z passes,
 // 32 consecutive x-lines for the x pass) staged in shared memory as
 // [position][pencil] (row stride 33: conflict-free both ways), an output
-// tile of the same shape, the doubled kernel row c in shared memory, 8 warps.
+// tile of the same shape, the doubled kernel row c in shared memory.
 // Lane = pencil; a warp computes 16 consecutive outputs at a time with the
 // kernel values in a 24-register window over blocks of 8 inputs: 8 shared
-// loads plus 6 16-byte broadcast loads per 128 FMAs.
+// loads plus 6 16-byte broadcast loads per 128 FMAs.  The CTA has as many
+// warps (4 to 12) as divide its output chunks most evenly (circ_warps): 19
+// chunks of n = 301 take 10 warps in two rounds, 5 chunks of n = 75 take 5.
+// The tile and the kernel row arrive by asynchronous 4-byte copies
+// (cp.async, zero-filled past the edges): every copy of a thread is in
+// flight at once, so staging costs about one memory round trip.
 // Accesses are scalar and coalesced (32 consecutive floats per warp), so no
 // alignment of nx is assumed; totals take scalar L2 reductions.
 //
@@ -26,6 +31,8 @@
 // result s_hi + s_lo carries the derivative to about twice FP32's precision,
 // so only the FP32 storage of the fields limits accuracy.  Chunks of 8 outputs
 // (registers), 10 FP32 operations per multiply-add.
+#include <cstdlib>
+
 #include "fft_pass.cuh"
 
 namespace es {
@@ -36,7 +43,33 @@ constexpr int ROW = TP + 1;     // shared row stride
 constexpr int OB = 16;          // outputs per warp chunk
 constexpr int JB = 8;           // inputs per block
 constexpr int KOFF = 16;        // least front padding of the kernel row (the window reaches OB - 1 before it)
-constexpr int CTHREADS = 256;
+constexpr int CMAXW = 12;                // most warps per CTA
+constexpr int CTHREADS = 32 * CMAXW;
+
+// warps for a CTA of `chunks` output chunks: the most even split (fewest idle
+// warp-rounds), ties to the count nearest 8
+inline int circ_warps(int chunks)
+{
+    int best = 8;
+    double be = -1.0;
+    for (int w = 4; w <= CMAXW; ++w) {
+        const int rounds = (chunks + w - 1) / w;
+        const double eff = (double)chunks / (double)(rounds * w);
+        if (eff > be + 1e-9 || (eff > be - 1e-9 && std::abs(w - 8) < std::abs(best - 8))) {
+            be = eff;
+            best = w;
+        }
+    }
+    return best;
+}
+
+// asynchronous 4-byte copy global -> shared; ok == false writes a zero and reads nothing
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __host__ __device__ inline int circ_pad(int n) { return (n + OB - 1) / OB * OB; }
 
@@ -99,7 +132,8 @@ __device__ __forceinline__ void circ_convolve(const float* tile, Emit emit, cons
 {
     constexpr int W = OBV + JB;  // window length, a multiple of 4
     const int np = circ_pad(n), koff = circ_koff(n);
-    for (int g = warp; g < np / OBV; g += CTHREADS / 32) {
+    const int nw = blockDim.x >> 5;
+    for (int g = warp; g < np / OBV; g += nw) {
         const int i0 = g * OBV;
         float acc[OBV], lo[OBV];
 #pragma unroll
@@ -155,10 +189,10 @@ __device__ __forceinline__ void circ_convolve(const float* tile, Emit emit, cons
 __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n, int tid)
 {
     const int len = circ_row_len(n), koff = circ_koff(n);
-    for (int s = tid; s < len; s += CTHREADS) {
+    for (int s = tid; s < len; s += blockDim.x) {
         int k = (s - koff) % n;
         if (k < 0) k += n;
-        cw[s] = __ldg(c + k);
+        cp_async4(cw + s, c + k, true);
     }
 }
 
@@ -195,12 +229,12 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
     pdl_begin(p.pdl);
     load_kernel_row(cw, J.sign > 0 ? p.ckp : p.ckm, n, tid);
     if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
-    for (int it = tid; it < np * TP; it += CTHREADS) {
+    for (int it = tid; it < np * TP; it += blockDim.x) {
         const int pos = it / TP, c = it % TP;
-        float v = 0.f;
-        if (pos < n && x0 + c < p.nx) v = __ldg(J.src + off + base0 + c + (size_t)pos * est);
-        tile[pos * ROW + c] = v;
+        const bool ok = pos < n && x0 + c < p.nx;
+        cp_async4(tile + pos * ROW + c, J.src + off + (ok ? base0 + c + (size_t)pos * est : 0), ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     if constexpr (DIRECT) {
         if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
@@ -220,7 +254,7 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_strided(const __grid_constan
             tile, [&](int pos, float d) { out[pos * ROW + lane] = d; }, cw, cl, n, warp, lane);
         __syncthreads();
         if (p.pdl == 1) pdl_wait();
-        for (int it = tid; it < n * TP; it += CTHREADS) {
+        for (int it = tid; it < n * TP; it += blockDim.x) {
             const int pos = it / TP, c = it % TP;
             const int x = x0 + c;
             if (x >= p.nx) continue;
@@ -252,18 +286,19 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     // the tile's lines are one contiguous block of nl * n floats
     const float* src = J.src + off + (size_t)line0 * n;
-    for (int e = tid; e < np * ROW; e += CTHREADS) tile[e] = 0.f;  // rows and lines past the edges
+    for (int e = tid; e < np * ROW; e += blockDim.x) tile[e] = 0.f;  // rows and lines past the edges
     __syncthreads();
-    for (int e = tid; e < nl * n; e += CTHREADS) {
+    for (int e = tid; e < nl * n; e += blockDim.x) {
         const int r = e / n, pos = e % n;
-        tile[pos * ROW + r] = __ldg(src + e);
+        cp_async4(tile + pos * ROW + r, src + e, true);
     }
+    cp_async_wait_all();
     __syncthreads();
     circ_convolve<COMP, COMP ? 8 : OB>(
         tile, [&](int pos, float d) { out[pos * ROW + lane] = d; }, cw, cl, n, warp, lane);
     __syncthreads();
     if (p.pdl == 1) pdl_wait();
-    for (int e = tid; e < nl * n; e += CTHREADS) {
+    for (int e = tid; e < nl * n; e += blockDim.x) {
         const int r = e / n, pos = e % n;
         const int line = line0 + r;
         epilogue_one(p, J, (size_t)line * n + pos, pos, pos, line % p.ny, line / p.ny, out[pos * ROW + r], off,
@@ -295,10 +330,11 @@ cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
 {
     if (p.n < 2 || p.n > CIRC_MAX_N || !p.ckp || !p.ckm) return cudaErrorInvalidValue;
     if (p.comp && (!p.ckp_lo || !p.ckm_lo)) return cudaErrorInvalidValue;
+    const int threads = 32 * circ_warps(circ_pad(p.n) / (p.comp ? 8 : OB));
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((unsigned)((lines + TP - 1) / TP) * p.nsim, p.njobs);
-        return launch_pass_kernel(p.comp ? circ_x<true> : circ_x<false>, grid, CTHREADS,
+        return launch_pass_kernel(p.comp ? circ_x<true> : circ_x<false>, grid, threads,
                                   circ_smem(p.n, p.comp != 0, true), st, p);
     }
     const int ntx = (p.nx + TP - 1) / TP;
@@ -307,9 +343,9 @@ cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
     const bool direct = p.n >= CIRC_DIRECT_N;
     const size_t smem = circ_smem(p.n, p.comp != 0, !direct);
     if (direct)
-        return launch_pass_kernel(p.comp ? circ_strided<true, true> : circ_strided<false, true>, grid, CTHREADS,
-                                  smem, st, p);
-    return launch_pass_kernel(p.comp ? circ_strided<true, false> : circ_strided<false, false>, grid, CTHREADS, smem,
+        return launch_pass_kernel(p.comp ? circ_strided<true, true> : circ_strided<false, true>, grid, threads, smem,
+                                  st, p);
+    return launch_pass_kernel(p.comp ? circ_strided<true, false> : circ_strided<false, false>, grid, threads, smem,
                               st, p);
 }
 

@@ -27,6 +27,7 @@ struct es_sur {
     float* scale;          // [4]
     float scale_h[4] = {1.f, 1.f, 1.f, 1.f};  // host copy (GEMM alpha of the fused inference output)
     __nv_bfloat16 *X, *H1b, *H2b, *Zb, *dUb, *dAb, *dH2b, *dH1b;
+    __nv_bfloat16 *ZT, *dUT;  // z^T [6K][B] and dU^T [D][B]: K-major operands of dWd = z^T dU
     float *H1, *H2, *A, *U, *dZ, *dA, *dH2, *dH1, *loss, *acc;
     int t = 0;
     // inference copy of the decoder, K-major for the tcgen05 GEMM: WdT [D][6K],
@@ -59,16 +60,33 @@ int check_batch(const es_sur* s, const void* pos, const void* mt, int B)
     return ES_OK;
 }
 
-// forward through the decoder: s->U = z Wd (normalized units).  For inference
-// (out != nullptr) the decoder product runs K-major on the tcgen05 tensor cores
-// (z WdT^T), one call per output component writing out[:, c D/4 ...] directly
-// with that component's scale as alpha.
+// The K-major copy of the decoder (WdT [D][6K]), rebuilt from the BF16 mirror
+// whenever the parameters have changed since (once per Adam step in training).
+int ensure_wdt(es_sur* s)
+{
+    if (!s->WdT && cudaMalloc(&s->WdT, sizeof(__nv_bfloat16) * 6 * s->K * s->D) != cudaSuccess) {
+        cudaGetLastError();
+        s->WdT = nullptr;
+        return ES_ERR_OOM;
+    }
+    if (s->wdt_ver != s->ver) {
+        CKS(transpose_bf16(s->pb + s->oWd, 6LL * s->K, s->D, s->WdT, s->st));
+        s->wdt_ver = s->ver;
+    }
+    return ES_OK;
+}
+
+// forward through the decoder on the tcgen05 tensor cores (both operands
+// K-major: z [B][6K] and WdT [D][6K]): s->U = z Wd in normalized units, or for
+// inference (out != nullptr) one call per output component writing
+// out[:, c D/4 ...] directly with that component's scale as alpha.
 int forward(es_sur* s, const float* pos, const float* mt, int B, float* out = nullptr)
 {
+    int rc = ensure_wdt(s);
+    if (rc != ES_OK) return rc;
     const __nv_bfloat16* W1 = s->pb + s->oW1;
     const __nv_bfloat16* W2 = s->pb + s->oW2;
     const __nv_bfloat16* W3 = s->pb + s->oW3;
-    const __nv_bfloat16* Wd = s->pb + s->oWd;
     CKS(sur_features(pos, B, s->cfg.nfreq, s->F, s->X, s->st));
     CKS(gemm_bf16(B, s->H, s->F, s->X, s->F, false, W1, s->H, false, s->H1, s->H, 1.f, 0.f, 1, s->st));
     CKS(sur_bias_act(s->H1, s->p + s->ob1, B, s->H, true, s->H1b, s->st));
@@ -83,8 +101,8 @@ int forward(es_sur* s, const float* pos, const float* mt, int B, float* out = nu
             CKS(gemm_bf16(B, (int)Dc, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT + (size_t)c * Dc * 6 * s->K, 6 * s->K,
                           true, out + (size_t)c * Dc, (int)s->D, s->scale_h[c], 0.f, 1, s->st));
     } else
-        CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, Wd, (int)s->D, false, s->U, (int)s->D, 1.f, 0.f,
-                      1, s->st));
+        CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT, 6 * s->K, true, s->U, (int)s->D, 1.f,
+                      0.f, 1, s->st));
     return ES_OK;
 }
 
@@ -95,8 +113,11 @@ int backward(es_sur* s, const float* mt, int B)
     const __nv_bfloat16* W2 = s->pb + s->oW2;
     const __nv_bfloat16* W3 = s->pb + s->oW3;
     const __nv_bfloat16* Wd = s->pb + s->oWd;
-    // decoder: dWd = z^T dU, dz = dU Wd^T (long K = D: split-K)
-    CKS(gemm_bf16(K6, D, B, s->Zb, K6, true, s->dUb, D, false, s->g + s->oWd, D, 1.f, 0.f, 1, s->st));
+    // decoder: dWd = z^T dU through the K-major transposes (both on tcgen05), dz = dU Wd^T
+    // (long K = D: split-K)
+    CKS(transpose_bf16(s->Zb, B, K6, s->ZT, s->st));
+    CKS(transpose_bf16(s->dUb, B, D, s->dUT, s->st));
+    CKS(gemm_bf16(K6, D, B, s->ZT, B, false, s->dUT, B, true, s->g + s->oWd, D, 1.f, 0.f, 1, s->st));
     const int split = (int)std::max<long long>(1, std::min<long long>(256, s->D / 2048));
     CKS(gemm_bf16(B, K6, D, s->dUb, D, false, Wd, D, true, s->dZ, K6, 1.f, 0.f, split, s->st));
     CKS(sur_contract(mt, s->dZ, B, s->K, s->dA, s->dAb, s->st));
@@ -148,7 +169,7 @@ int es_sur_create(const es_sur_config* cfg, es_sur** out)
     s->P = o;
     const size_t B = s->B, P = s->P, H = s->H, K = s->K, D = s->D, F = s->F;
     const size_t f32 = 4 * (4 * P + 4 + B * (2 * H + K + D + 6 * K + K + 2 * H + 2) + 128);
-    const size_t b16 = 2 * (P + B * (F + 2 * H + 6 * K + D + K + 2 * H)) + 1024;
+    const size_t b16 = 2 * (P + B * (F + 2 * H + 6 * K + D + K + 2 * H) + B * (6 * K + D)) + 2048;
     if (cudaMalloc(&s->pool, f32 + b16) != cudaSuccess) {
         delete s;
         return ES_ERR_OOM;
@@ -181,6 +202,8 @@ int es_sur_create(const es_sur_config* cfg, es_sur** out)
     s->dAb = takeb(B * K);
     s->dH2b = takeb(B * H);
     s->dH1b = takeb(B * H);
+    s->ZT = takeb(6 * K * B);
+    s->dUT = takeb(D * B);
     const float ones[4] = {1.f, 1.f, 1.f, 1.f};
     cudaError_t e = cudaMemcpy(s->scale, ones, sizeof ones, cudaMemcpyHostToDevice);
     // N(0, 1/fan_in) weights, zero biases, decoder scaled so the first outputs are small
@@ -266,15 +289,6 @@ int es_sur_predict(es_sur* s, const float* pos, const float* mt, int B, float* o
     if (rc != ES_OK) return rc;
     if (!out || !dev_ptr(out)) return ES_ERR_ARG;
     cudaGetLastError();
-    if (!s->WdT && cudaMalloc(&s->WdT, sizeof(__nv_bfloat16) * 6 * s->K * s->D) != cudaSuccess) {
-        cudaGetLastError();
-        s->WdT = nullptr;
-        return ES_ERR_OOM;
-    }
-    if (s->wdt_ver != s->ver) {
-        CKS(transpose_bf16(s->pb + s->oWd, 6LL * s->K, s->D, s->WdT, s->st));
-        s->wdt_ver = s->ver;
-    }
     if ((rc = forward(s, pos, mt, B, out)) != ES_OK) return rc;
     return ES_OK;
 }
@@ -309,8 +323,14 @@ int es_sur_train_step(es_sur* s, const float* pos, const float* mt, const float*
     CKS(sur_loss(s->U, target, s->scale, B, s->D / 4, 1e-30f, s->dUb, s->loss, s->acc, nullptr, s->st));
     if ((rc = backward(s, mt, B)) != ES_OK) return rc;
     s->t += 1;
-    CKS(sur_adam(s->p, s->g, s->m, s->v, s->P, lr, 0.9f, 0.999f, 1e-8f, s->t, s->pb, s->st));
+    // the MLP's parameters, then the decoder (the last segment) with its K-major copy refreshed
+    // in the same pass
+    const size_t K6 = 6 * (size_t)s->K;
+    CKS(sur_adam(s->p, s->g, s->m, s->v, s->oWd, lr, 0.9f, 0.999f, 1e-8f, s->t, s->pb, s->st));
+    CKS(sur_adam_t(s->p + s->oWd, s->g + s->oWd, s->m + s->oWd, s->v + s->oWd, (long long)K6, s->D, lr, 0.9f, 0.999f,
+                   1e-8f, s->t, s->pb + s->oWd, s->WdT, s->st));
     s->ver += 1;
+    s->wdt_ver = s->ver;
     if (loss) {
         CKS(cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToHost, s->st));
         CKS(cudaStreamSynchronize(s->st));

@@ -15,10 +15,12 @@
 //       frees each stage and, at the end of a tile, hands the accumulator to
 //       the epilogue;
 //   warps 2-5: epilogue -- warp w owns TMEM lanes (tile rows)
-//       32 (w mod 4) .. +31, reads 32 columns at a time with tcgen05.ld and
-//       writes alpha * acc + beta * C (split_k > 1: atomically adds
-//       alpha * acc onto a C that already holds beta * C), then returns the
-//       accumulator; the next tile's MMAs run in the other one meanwhile.
+//       32 (w mod 4) .. +31, reads 32 columns at a time with tcgen05.ld
+//       (lane = row), turns the 32 x 32 block around in its own shared
+//       buffer so that each store instruction covers four whole 128-byte row
+//       segments, and writes alpha * acc + beta * C (split_k > 1: atomically
+//       adds alpha * acc onto a C that already holds beta * C), then returns
+//       the accumulator; the next tile's MMAs run in the other one meanwhile.
 // Rows, columns and K past the matrix edge are zero-filled by TMA and masked
 // in the epilogue.  Every mbarrier wait gives up after WAIT_NS of global
 // time, records the role that gave up in a device status word (read and
@@ -45,7 +47,10 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = TM * TK * 2;
 constexpr int B_BYTES = TN * TK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack for the 1024-byte swizzle atoms
+constexpr int EPI_LD = 36;  // row stride (floats) of an epilogue warp's 32 x 32 staging block: 16-byte rows
+constexpr int EPI_BYTES = 4 * 32 * EPI_LD * 4;
+// ring + staging + alignment slack for the 1024-byte swizzle atoms
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr int THREADS = 192;
 constexpr unsigned TMEM_COLS = 2 * TN;  // two accumulators
 constexpr unsigned long long WAIT_NS = 2000000000ull;
@@ -277,22 +282,32 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const int row = mi * TM + q * 32 + lane, n0 = ni * TN;
-            float* crow = C + (size_t)row * ldc;
+            const int n0 = ni * TN, row0 = mi * TM + q * 32;
+            // this warp's staging block: row r (TMEM lane) at stage + r * EPI_LD
+            float* stage = reinterpret_cast<float*>(dyn + (base - smem_u32(dyn)) + STAGES * STAGE_BYTES) +
+                           q * 32 * EPI_LD;
             for (int c0 = 0; c0 < TN; c0 += 32) {
                 if (n0 + c0 >= N) break;  // uniform over the warp
-                __syncwarp();               // lanes meet again after the row mask below
+                __syncwarp();               // the previous block's reads of the staging rows are done
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + c0), r);
-                if (row >= M) continue;
-                const int ncol = min(32, N - n0 - c0);
-                float* p = crow + n0 + c0;
-                if (vec && ncol == 32) {
+                float4* srow = reinterpret_cast<float4*>(stage + lane * EPI_LD);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float4 v = make_float4(alpha * __uint_as_float(r[j]), alpha * __uint_as_float(r[j + 1]),
-                                               alpha * __uint_as_float(r[j + 2]), alpha * __uint_as_float(r[j + 3]));
-                        float4* dst = reinterpret_cast<float4*>(p + j);
+                for (int j = 0; j < 8; ++j)
+                    srow[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
+                                          alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+                __syncwarp();
+                // lane l stores columns 4 (l mod 8) .. +3 of row 4 i + l / 8: a warp instruction writes
+                // four whole 128-byte row segments
+                const int cc = n0 + c0 + 4 * (lane & 7);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3), grow = row0 + rr;
+                    if (grow >= M || cc >= N) continue;
+                    float4 v = *reinterpret_cast<const float4*>(stage + rr * EPI_LD + 4 * (lane & 7));
+                    float* p = C + (size_t)grow * ldc + cc;
+                    if (vec && cc + 4 <= N) {
+                        float4* dst = reinterpret_cast<float4*>(p);
                         if (atomic) {
                             atomicAdd(dst, v);
                         } else {
@@ -305,14 +320,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                             }
                             *dst = v;
                         }
-                    }
-                } else {
+                    } else {
+                        const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (j < ncol) {
-                            const float v = alpha * __uint_as_float(r[j]);
-                            if (atomic) atomicAdd(p + j, v);
-                            else p[j] = beta != 0.f ? v + beta * p[j] : v;
+                        for (int k = 0; k < 4; ++k) {
+                            if (cc + k >= N) break;
+                            if (atomic) atomicAdd(p + k, e[k]);
+                            else p[k] = beta != 0.f ? e[k] + beta * p[k] : e[k];
                         }
                     }
                 }

@@ -50,5 +50,11 @@ cudaError_t sur_colsum(const float* G, int B, int N, float* db, cudaStream_t st)
 // Adam step (bias-corrected, lr, b1, b2, eps) on FP32 params, refreshing the BF16 copy (may be null)
 cudaError_t sur_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
                      int t, __nv_bfloat16* pb, cudaStream_t st);
+// The same step on a row-major [rows][cols] block (the decoder; cols a multiple
+// of 4, 16-byte aligned), writing the BF16 copy both row-major (pb) and
+// transposed (pt, [cols][rows]) -- one pass over the parameters instead of a
+// step plus a transpose.
+cudaError_t sur_adam_t(float* p, const float* g, float* m, float* v, long long rows, long long cols, float lr,
+                       float b1, float b2, float eps, int t, __nv_bfloat16* pb, __nv_bfloat16* pt, cudaStream_t st);
 
 }  // namespace es

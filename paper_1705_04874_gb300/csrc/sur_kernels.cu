@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -177,18 +178,99 @@ __global__ void colsum_kernel(const float* G, int B, int N, float* db)
     db[n] = s;
 }
 
+// one Adam update (bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t); returns the new parameter
+__device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                          float eps, float c1, float c2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p = p - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    return p;
+}
+
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
                             float eps, float c1, float c2, __nv_bfloat16* pb)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        float pi = p[i], mi = m[i], vi = v[i];
+        adam_one(pi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
         m[i] = mi;
         v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         p[i] = pi;
         if (pb) pb[i] = __float2bfloat16(pi);
+    }
+}
+
+__device__ __forceinline__ void adam_four(float4& p, float4 g, float4& m, float4& v, float lr, float b1, float b2,
+                                          float eps, float c1, float c2)
+{
+    adam_one(p.x, g.x, m.x, v.x, lr, b1, b2, eps, c1, c2);
+    adam_one(p.y, g.y, m.y, v.y, lr, b1, b2, eps, c1, c2);
+    adam_one(p.z, g.z, m.z, v.z, lr, b1, b2, eps, c1, c2);
+    adam_one(p.w, g.w, m.w, v.w, lr, b1, b2, eps, c1, c2);
+}
+
+__device__ __forceinline__ uint2 pack_bf16x4(float4 p)
+{
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(p.x, p.y), hi = __floats2bfloat162_rn(p.z, p.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
+// four parameters per thread and iteration (n4 groups of four, 16-byte aligned)
+__global__ void adam4_kernel(float4* p, const float4* g, float4* m, float4* v, size_t n4, float lr, float b1,
+                             float b2, float eps, float c1, float c2, uint2* pb)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        float4 pi = p[i], mi = m[i], vi = v[i];
+        adam_four(pi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
+        m[i] = mi;
+        v[i] = vi;
+        p[i] = pi;
+        if (pb) pb[i] = pack_bf16x4(pi);
+    }
+}
+
+// 64 x 64 tiles of a row-major [rows][cols] block: the update and the
+// row-major BF16 copy four columns per thread, the transposed copy through a
+// shared [column][row] tile, four rows per thread (8-byte stores)
+constexpr int AT = 64, AT_LD = AT + 4;
+__global__ void adam_t_kernel(float* p, const float* g, float* m, float* v, long long rows, long long cols, float lr,
+                              float b1, float b2, float eps, float c1, float c2, __nv_bfloat16* pb,
+                              __nv_bfloat16* pt)
+{
+    __shared__ __align__(16) __nv_bfloat16 tt[AT][AT_LD];
+    const long long c0 = (long long)blockIdx.x * AT, r0 = (long long)blockIdx.y * AT;
+    const int cq = threadIdx.x & 15, rq = threadIdx.x >> 4;  // 16 column quads x 16 rows per sweep
+    for (int i = rq; i < AT; i += 16) {
+        const long long r = r0 + i, c = c0 + 4 * cq;
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rows && c < cols) {
+            const size_t k = (size_t)r * cols + c;
+            pi = *reinterpret_cast<const float4*>(p + k);
+            float4 mi = *reinterpret_cast<const float4*>(m + k), vi = *reinterpret_cast<const float4*>(v + k);
+            adam_four(pi, *reinterpret_cast<const float4*>(g + k), mi, vi, lr, b1, b2, eps, c1, c2);
+            *reinterpret_cast<float4*>(m + k) = mi;
+            *reinterpret_cast<float4*>(v + k) = vi;
+            *reinterpret_cast<float4*>(p + k) = pi;
+            *reinterpret_cast<uint2*>(pb + k) = pack_bf16x4(pi);
+        }
+        tt[4 * cq][i] = __float2bfloat16(pi.x);
+        tt[4 * cq + 1][i] = __float2bfloat16(pi.y);
+        tt[4 * cq + 2][i] = __float2bfloat16(pi.z);
+        tt[4 * cq + 3][i] = __float2bfloat16(pi.w);
+    }
+    __syncthreads();
+    for (int j = rq; j < AT; j += 16) {
+        const long long c = c0 + j, r = r0 + 4 * cq;
+        if (c >= cols || r >= rows) continue;
+        const uint2 q = *reinterpret_cast<const uint2*>(&tt[j][4 * cq]);
+        __nv_bfloat16* dst = pt + (size_t)c * rows + r;
+        if (r + 4 <= rows && (rows & 3) == 0) {
+            *reinterpret_cast<uint2*>(dst) = q;
+        } else {
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+            for (int k = 0; k < 4 && r + k < rows; ++k) dst[k] = e[k];
+        }
     }
 }
 
@@ -311,7 +393,32 @@ cudaError_t sur_adam(float* p, const float* g, float* m, float* v, size_t n, flo
                      int t, __nv_bfloat16* pb, cudaStream_t st)
 {
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-    adam_kernel<<<blocks_for(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2, pb);
+    const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                         reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+    if (n % 4 == 0 && (al & 15) == 0 && (reinterpret_cast<uintptr_t>(pb) & 7) == 0) {
+        adam4_kernel<<<blocks_for(n / 4), 256, 0, st>>>(
+            reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g), reinterpret_cast<float4*>(m),
+            reinterpret_cast<float4*>(v), n / 4, lr, b1, b2, eps, c1, c2, reinterpret_cast<uint2*>(pb));
+    } else {
+        adam_kernel<<<blocks_for(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2, pb);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sur_adam_t(float* p, const float* g, float* m, float* v, long long rows, long long cols, float lr,
+                       float b1, float b2, float eps, int t, __nv_bfloat16* pb, __nv_bfloat16* pt, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                         reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+    if (cols % 4 || (al & 15) || (reinterpret_cast<uintptr_t>(pb) & 7) || (reinterpret_cast<uintptr_t>(pt) & 7) ||
+        !pb || !pt)
+        return cudaErrorInvalidValue;
+    const long long gx = (cols + AT - 1) / AT, gy = (rows + AT - 1) / AT;
+    if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_t_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(p, g, m, v, rows, cols, lr, b1, b2, eps, c1, c2,
+                                                                     pb, pt);
     return cudaGetLastError();
 }
 

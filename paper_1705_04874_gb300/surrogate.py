@@ -300,24 +300,39 @@ def calibrate_gate(sur, pos_n, G, n_val=4, threshold=0.05, margin=0.8, seed=7):
     return errs.max(axis=1) <= margin * threshold, errs
 
 
-def serve(sur, pos_n, trusted, loc, mt, solver_model, locations, nt, dt, rcv, wavelet, batch_solver=16):
+def serve(sur, pos_n, trusted, loc, mt, solver_model, locations, nt, dt, rcv, wavelet, batch_solver=16, out=None):
     """Seismograms for sources (location index, moment tensor): the surrogate
     where the gate trusts the location, the solver (batched runs) elsewhere.
-    Returns (traces CUDA [B][4][n_rcv][nt], used_solver bool [B])."""
+    out: optional contiguous CUDA float32 [B][4][n_rcv][nt] to fill (a reused
+    serving buffer).  Returns (traces CUDA [B][4][n_rcv][nt], used_solver bool
+    [B])."""
     import torch
     B = len(loc)
     n_rcv = len(rcv)
-    out = torch.empty((B, 4, n_rcv, nt), device="cuda")
+    if out is None:
+        out = torch.empty((B, 4, n_rcv, nt), device="cuda")
+    elif tuple(out.shape) != (B, 4, n_rcv, nt) or not out.is_contiguous() or out.dtype != torch.float32:
+        raise ValueError("serve: out must be a contiguous float32 [B][4][n_rcv][nt] CUDA tensor")
+    flat = out.view(B, -1)
     use_sur = trusted[np.asarray(loc)]
     idx = np.nonzero(use_sur)[0]
-    for s in range(0, len(idx), sur.max_batch):
-        part = idx[s:s + sur.max_batch]
-        m = (len(part) + 7) // 8 * 8
-        pp = np.concatenate([part, np.repeat(part[:1], m - len(part))])
-        p = torch.from_numpy(pos_n[np.asarray(loc)[pp]]).cuda()
-        mm = torch.from_numpy(np.asarray(mt, np.float32)[pp]).cuda()
-        y = sur.predict(p, mm)
-        out[torch.from_numpy(part).cuda()] = y[:len(part)].view(len(part), 4, n_rcv, nt)
+    if len(idx):
+        # the inputs of every trusted source in one copy each; a run of consecutive sources
+        # (all of them when every location is trusted) is predicted straight into the output
+        p_all = torch.from_numpy(np.ascontiguousarray(pos_n[np.asarray(loc)[idx]], np.float32)).cuda()
+        m_all = torch.from_numpy(np.ascontiguousarray(np.asarray(mt, np.float32)[idx])).cuda()
+        run = idx[-1] - idx[0] == len(idx) - 1
+        for s in range(0, len(idx), sur.max_batch):
+            part = idx[s:s + sur.max_batch]
+            n = len(part)
+            if run and n % 8 == 0:
+                sur.predict(p_all[s:s + n], m_all[s:s + n], out=flat[part[0]:part[0] + n])
+                continue
+            pad = (n + 7) // 8 * 8 - n
+            p = torch.cat([p_all[s:s + n], p_all[s:s + 1].expand(pad, 3)]).contiguous()
+            mm = torch.cat([m_all[s:s + n], m_all[s:s + 1].expand(pad, 6)]).contiguous()
+            y = sur.predict(p, mm)
+            out[torch.from_numpy(part).cuda()] = y[:n].view(n, 4, n_rcv, nt)
     rest = np.nonzero(~use_sur)[0]
     rcv_d = torch.from_numpy(np.ascontiguousarray(rcv, np.int32)).cuda()
     for s in range(0, len(rest), batch_solver):

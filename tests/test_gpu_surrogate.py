@@ -120,6 +120,95 @@ def test_loss_and_gradients_match_oracle(env):
         s.close()
 
 
+def test_train_step_matches_oracle_adam(env):
+    """One train step against the oracle's Adam step taken from its own FP64
+    gradient (BF16-rounded weights).  The first Adam step moves a parameter by
+    lr g / (|g| + eps), so wherever the gradient's sign is certain the GPU's
+    update must equal the oracle's to FP32 rounding, and no parameter may move
+    by more than lr.  The decoder has 96 rows (ragged 64-row tiles of the
+    fused step).  Then predict() must run on the updated decoder: its K-major
+    copy is refreshed by the step itself."""
+    es, sur, torch = env
+    from oracle import surrogate as osur
+    cfg = dict(nfreq=2, hidden=64, latent=16, n_rcv=4, nt=16)
+    s = sur.Surrogate(cfg["n_rcv"], cfg["nt"], nfreq=2, hidden=64, latent=16, max_batch=16, seed=3)
+    try:
+        rng = np.random.default_rng(11)
+        lay, P, F, D = osur.layout(**cfg)
+        params = (rng.standard_normal(P) * 0.2).astype(np.float32)
+        s.set_params(params)
+        scale = [1.5, 0.7, 0.9, 1.1]
+        s.set_output_scale(scale)
+        B, lr = 16, 2e-2
+        pos = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+        mt = rng.standard_normal((B, 6)).astype(np.float32)
+        tgt = rng.standard_normal((B, D)).astype(np.float32)
+        cu = lambda a: torch.from_numpy(a).cuda()
+        s.predict(cu(pos), cu(mt))  # the K-major copy of the initial decoder exists before the step
+        s.train_step(cu(pos), cu(mt), cu(tgt), lr)
+        after = s.get_params().astype(np.float64)
+
+        def bf16(x):
+            out = np.asarray(x, np.float64).copy()
+            r = torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy()
+            for name in ("W1", "W2", "W3", "Wd"):
+                o, shp = lay[name]
+                out[o:o + int(np.prod(shp))] = r[o:o + int(np.prod(shp))]
+            return out
+
+        _, _, og = osur.loss_and_grads(bf16(params), cfg, pos, mt, tgt, scale)
+        exp, _, _ = osur.adam_step(params.astype(np.float64), og, 0.0, 0.0, 1, lr)
+        moved = after - params.astype(np.float64)
+        assert np.abs(moved).max() <= lr * (1 + 1e-3)
+        # The GPU's gradient is within tol * |g| of the oracle's (the bound of the gradient test), so
+        # an element larger than that keeps its sign and must take the oracle's step exactly; below
+        # it BF16 rounding may flip a sign, which at most 5 % of the elements may show.
+        tol = {"W1": 6e-2, "b1": 6e-2}
+        for name, (o, shp) in lay.items():
+            n = int(np.prod(shp))
+            g = og[o:o + n]
+            dev = np.abs(after[o:o + n] - exp[o:o + n])
+            sure = np.abs(g) > tol.get(name, 3e-2) * np.linalg.norm(g)
+            assert not sure.any() or dev[sure].max() <= 1e-3 * lr, name
+            nz = g != 0
+            assert np.mean(dev[nz] <= 1e-3 * lr) >= 0.95, (name, np.mean(dev[nz] <= 1e-3 * lr))
+        y = s.predict(cu(pos), cu(mt)).cpu().numpy()
+        ref = osur.forward(bf16(after.astype(np.float32)), cfg, pos, mt, scale)["Y"]
+        stale = osur.forward(bf16(np.concatenate([after[:lay["Wd"][0]], params[lay["Wd"][0]:]]).astype(np.float32)),
+                             cfg, pos, mt, scale)["Y"]
+        assert np.linalg.norm(ref - stale) > 5e-2 * np.linalg.norm(ref)  # the step moved the decoder visibly
+        assert np.linalg.norm(y - ref) <= 1e-2 * np.linalg.norm(ref)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("n_src", [40, 37])
+def test_serve_trusted_sources(env, n_src):
+    """Every location trusted: serve() predicts runs of consecutive sources
+    straight into the caller's buffer (a ragged tail through a padded batch);
+    the result equals predict() on the same inputs, bit for bit."""
+    es, sur, torch = env
+    s = sur.Surrogate(2, 16, nfreq=2, hidden=32, latent=8, max_batch=16, seed=2)
+    try:
+        rng = np.random.default_rng(n_src)
+        pos_n = rng.uniform(-1, 1, (5, 3)).astype(np.float32)
+        loc = rng.integers(0, 5, n_src)
+        mts = rng.standard_normal((n_src, 6))
+        buf = torch.full((n_src, 4, 2, 16), float("nan"), device="cuda")
+        out, used = sur.serve(s, pos_n, np.ones(5, bool), loc, mts, None, None, 16, 0.0, np.zeros((2, 3), np.int32),
+                              None, out=buf)
+        assert out.data_ptr() == buf.data_ptr() and not used.any()
+        for b in range(0, n_src, 16):
+            n = min(16, n_src - b)
+            k = (n + 7) // 8 * 8
+            idx = np.concatenate([np.arange(b, b + n), np.full(k - n, b)])
+            ref = s.predict(torch.from_numpy(pos_n[loc[idx]]).cuda(),
+                            torch.from_numpy(mts[idx].astype(np.float32)).cuda())[:n]
+            assert torch.equal(out[b:b + n].reshape(n, -1), ref), b
+    finally:
+        s.close()
+
+
 def test_catalog_train_gate_serve(env):
     """Small marine model, 24 catalog locations: the surrogate learns their
     Green's functions from 144 solver runs (unit moment tensors), is trained

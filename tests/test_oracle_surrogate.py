@@ -44,3 +44,23 @@ def test_prediction_is_linear_in_the_moment_tensor():
              for c in range(6))
     assert np.allclose(y2, 2.5 * y1, rtol=1e-12, atol=0)
     assert np.allclose(ys, y1, rtol=1e-10, atol=1e-12)
+
+
+def test_adam_closed_forms():
+    """With a constant gradient the bias-corrected moments equal g and g^2 at
+    every step, so each of five steps moves a parameter by exactly
+    lr g / (|g| + eps); a gradient g followed by -g gives, at step 2,
+    m_hat = -0.01 g / 0.19 and v_hat = g^2 (0.001999 / 0.001999).  A dropped
+    bias correction, swapped decay rates or a sign error fails one of these."""
+    rng = np.random.default_rng(3)
+    p0 = rng.standard_normal(50)
+    g = rng.standard_normal(50) * np.logspace(-3, 2, 50)
+    lr, eps = 1e-3, 1e-8
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for t in range(1, 6):
+        p, m, v = osur.adam_step(p, g, m, v, t, lr, eps=eps)
+        assert np.allclose(p, p0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12)
+    p, m, v = osur.adam_step(p0, g, np.zeros(50), np.zeros(50), 1, lr, eps=eps)
+    p, m, v = osur.adam_step(p, -g, m, v, 2, lr, eps=eps)
+    step2 = lr * (-0.01 * g / 0.19) / (np.abs(g) + eps)
+    assert np.allclose(p, p0 - lr * g / (np.abs(g) + eps) - step2, rtol=0, atol=1e-12)
