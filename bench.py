@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm", "serve", "paper"])
+    ap.add_argument("--workload", default="256", choices=["256", "128", "surrogate", "configs", "gemm", "serve", "train", "paper"])
     ap.add_argument("--gemm-small", action="store_true", help="gemm workload: the decoder shape only")
     ap.add_argument("--sur-locations", type=int, default=682)
     ap.add_argument("--sur-epochs", type=int, default=150)
@@ -217,6 +217,8 @@ def main():
         return measure_gemm(args)
     if args.workload == "serve":
         return measure_serve(args)
+    if args.workload == "train":
+        return measure_train(args)
     if args.workload == "paper":
         return measure_paper(args)
     w = workload(args.workload)
@@ -484,6 +486,40 @@ def measure_serve(args):
     print(json.dumps({"metric": "seismograms/s", "value": round(n_src / (ms * 1e-3), 1),
                       "unit": "4C seismogram sets/s (network only)", "ms_per_10k": round(ms, 2),
                       "batches": n_batches, "dtype": "bf16/f32", "data": "synthetic"}))
+    return 0
+
+
+def measure_train(args):
+    """Training cost of the surrogate network alone: the C5 network shape (as --workload serve)
+    with its initial weights, a batch of 256 sources with synthetic targets of the C5 trace shape
+    (the cost does not depend on the values); --warmup then --steps Adam steps through
+    es_sur_train_step, timed with CUDA events.  Metric: milliseconds per Adam step."""
+    import torch
+    from paper_1705_04874_gb300 import surrogate as sur
+    torch.cuda.set_device(0)
+    s = sur.Surrogate(64, 1024, nfreq=9, hidden=768, latent=768, max_batch=256, seed=1)
+    rng = np.random.default_rng(4)
+    B = 256
+    pos = torch.from_numpy(rng.uniform(-1, 1, (B, 3)).astype(np.float32)).cuda()
+    mt = torch.from_numpy(rng.standard_normal((B, 6)).astype(np.float32)).cuda()
+    tgt = torch.from_numpy((1e-3 * rng.standard_normal((B, s.D))).astype(np.float32)).cuda()
+    s.set_output_scale([1e-3] * 4)
+    for _ in range(max(args.warmup, 0)):
+        s.train_step(pos, mt, tgt, 1e-4, want_loss=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.train_step(pos, mt, tgt, 1e-4, want_loss=False)
+    e1.record()
+    torch.cuda.synchronize()
+    sur.es_gemm_status()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    n_par = s.num_params()
+    s.close()
+    print(json.dumps({"metric": "ms per Adam step", "value": round(ms, 3), "unit": "ms", "higher_is_better": False,
+                      "batch": B, "params": n_par, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "bf16/f32", "data": "synthetic"}))
     return 0
 
 
