@@ -288,9 +288,16 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     const float* src = J.src + off + (size_t)line0 * n;
     for (int e = tid; e < np * ROW; e += blockDim.x) tile[e] = 0.f;  // rows and lines past the edges
     __syncthreads();
-    for (int e = tid; e < nl * n; e += blockDim.x) {
-        const int r = e / n, pos = e % n;
-        cp_async4(tile + pos * ROW + r, src + e, true);
+    // element e = r n + pos of the block; (r, pos) advance by blockDim.x without a division per element
+    const int bd = blockDim.x, dr = bd / n, dp = bd % n;
+    for (int r = tid / n, pos = tid % n; r < nl;) {
+        cp_async4(tile + pos * ROW + r, src + (size_t)r * n + pos, true);
+        pos += dp;
+        r += dr;
+        if (pos >= n) {
+            pos -= n;
+            ++r;
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -298,11 +305,16 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
         tile, [&](int pos, float d) { out[pos * ROW + lane] = d; }, cw, cl, n, warp, lane);
     __syncthreads();
     if (p.pdl == 1) pdl_wait();
-    for (int e = tid; e < nl * n; e += blockDim.x) {
-        const int r = e / n, pos = e % n;
+    // the slab index along x is sp + S (y + ny z) = sp + S line: the line goes in as y, with z = 0
+    for (int r = tid / n, pos = tid % n; r < nl;) {
         const int line = line0 + r;
-        epilogue_one(p, J, (size_t)line * n + pos, pos, pos, line % p.ny, line / p.ny, out[pos * ROW + r], off,
-                     soff);
+        epilogue_one(p, J, (size_t)line * n + pos, pos, pos, line, 0, out[pos * ROW + r], off, soff);
+        pos += dp;
+        r += dr;
+        if (pos >= n) {
+            pos -= n;
+            ++r;
+        }
     }
 }
 
