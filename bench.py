@@ -439,12 +439,13 @@ def gemm_tflops(sur, M, N, K, b_nk, reps=5):
 
 
 def measure_gemm(args):
-    """The surrogate's GEMM alone: the decoder product of 256 sources (256 x 262,144 x 4,608,
-    tcgen05), and 8192^3 on the tcgen05 and mma.sync paths."""
+    """The surrogate's GEMM alone: the decoder product of 256 and of 1024 sources (M x 262,144 x
+    4,608, tcgen05), and 8192^3 on the tcgen05 and mma.sync paths (--gemm-small: the first only)."""
     import torch
     from paper_1705_04874_gb300 import surrogate as sur
     torch.cuda.set_device(0)
     shapes = [("tcgen05_decoder_256x262144x4608", 256, 262144, 4608, True),
+              ("tcgen05_decoder_1024x262144x4608", 1024, 262144, 4608, True),
               ("tcgen05_8192", 8192, 8192, 8192, True), ("mma_sync_8192", 8192, 8192, 8192, False)]
     if args.gemm_small:
         shapes = shapes[:1]
@@ -457,13 +458,13 @@ def measure_serve(args):
     """Serving cost of the surrogate network alone: the C5 network shape (64 receivers x 1024
     samples, 3 -> 768 -> 768 -> 768 latent, 9 positional frequencies; 1.21 G parameters) with
     its initial weights (the cost does not depend on the values), 10,000 random sources in
-    batches of 256 through es_sur_predict.  Metric: seismogram sets per second."""
+    batches of 1024 (the serving batch) through es_sur_predict.  Metric: seismogram sets per second."""
     import torch
     from paper_1705_04874_gb300 import surrogate as sur
     torch.cuda.set_device(0)
-    s = sur.Surrogate(64, 1024, nfreq=9, hidden=768, latent=768, max_batch=256, seed=1)
+    s = sur.Surrogate(64, 1024, nfreq=9, hidden=768, latent=768, max_batch=1024, seed=1)
     rng = np.random.default_rng(3)
-    n_src, B = 10000, 256
+    n_src, B = 10000, 1024
     pos = torch.from_numpy(rng.uniform(-1, 1, (n_src + B, 3)).astype(np.float32)).cuda()
     mt = torch.from_numpy(rng.standard_normal((n_src + B, 6)).astype(np.float32)).cuda()
     out = torch.empty((B, s.D), device="cuda")
@@ -696,15 +697,19 @@ def measure_configs(args):
     return 0
 
 
-def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, gemm=True):
+def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, gemm=True, serve_batch=1024,
+                       train_batch=256):
     """The surrogate workflow on the 96^3 marine model (PML 10, 8 x 8 seabed
     receivers, 1024 samples, Ricker 30 Hz): a catalog of n_loc Latin-hypercube
     locations in the reservoir box whose 6 unit-moment responses come from
     6 n_loc batched solver runs; training on the GPU; the gate; n_src random
     sources (catalog location, random double couple) served by the surrogate
     where the gate trusts the location and by the solver elsewhere, each
-    checked against its exact reference.  Returns (summary dict, decoder
-    roofline dict or None)."""
+    checked against its exact reference.  Training takes batches of
+    train_batch sources, serving batches of serve_batch: the decoder product
+    reads its 2.4 GB of weights once per batch, so a wide serving batch turns
+    it from HBM-bound (256) to tensor-bound (1024).  Returns (summary dict,
+    decoder roofline dict or None)."""
     import torch
     from paper_1705_04874_gb300 import es, surrogate as sur
     torch.cuda.set_device(0)
@@ -726,10 +731,10 @@ def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, ge
     out["catalog_s"] = round(t_cat, 2)
     solver_rate = 6 * n_loc / t_cat  # seismogram sets per second, batched solver
     pos_n = sur.normalize_positions(locations, box)
-    s = sur.Surrogate(len(rcv), nt, nfreq=nfreq, hidden=hidden, latent=latent, max_batch=256, seed=1)
+    s = sur.Surrogate(len(rcv), nt, nfreq=nfreq, hidden=hidden, latent=latent, max_batch=serve_batch, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = sur.train(s, pos_n, G, epochs=epochs, lr=lr)
+    hist = sur.train(s, pos_n, G, epochs=epochs, lr=lr, batch=train_batch)
     torch.cuda.synchronize()
     out["train_s"] = round(time.perf_counter() - t0, 2)
     out["train_loss"] = [float(f"{hist[0]:.3e}"), float(f"{hist[-1]:.3e}")]
@@ -744,9 +749,10 @@ def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, ge
     # surrogate alone on all sources (rate of the network)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = torch.empty((256, 4 * len(rcv) * nt), device="cuda")
-    for b in range(0, n_src, 256):
-        idx = np.arange(b, min(n_src, b + 256))
+    SB = s.max_batch
+    res = torch.empty((SB, 4 * len(rcv) * nt), device="cuda")
+    for b in range(0, n_src, SB):
+        idx = np.arange(b, min(n_src, b + SB))
         k = (len(idx) + 7) // 8 * 8
         idx = np.concatenate([idx, np.repeat(idx[:1], k - len(idx))])
         s.predict(torch.from_numpy(pos_n[loc[idx]]).cuda(), torch.from_numpy(mts[idx].astype(np.float32)).cuda(),
@@ -782,38 +788,49 @@ def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, ge
                 "speedup_surrogate_vs_solver": round(sur_rate / solver_rate, 1),
                 "speedup_pipeline_vs_solver": round(pipe_rate / solver_rate, 1),
                 "network": {"hidden": hidden, "latent": latent, "nfreq": nfreq, "params": s.num_params(),
-                            "epochs": epochs, "lr": lr}})
+                            "epochs": epochs, "lr": lr, "train_batch": train_batch, "serve_batch": SB}})
     roof = None
     if gemm:
         # throughput of the network's GEMMs: tcgen05 (both operands K-major: inference decoder,
         # dZ), mma.sync (the other storage orders), and the decoder product at the served shape
         K6 = 6 * latent
+        dec_name = f"tcgen05_decoder_{SB}x{s.D}x{K6}"
         g = {"tcgen05_8192": round(gemm_tflops(sur, 8192, 8192, 8192, True), 1),
              "mma_sync_8192": round(gemm_tflops(sur, 8192, 8192, 8192, False), 1),
-             f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(sur, 256, s.D, K6, True), 1)}
+             f"tcgen05_decoder_256x{s.D}x{K6}": round(gemm_tflops(sur, 256, s.D, K6, True), 1),
+             dec_name: round(gemm_tflops(sur, SB, s.D, K6, True), 1)}
         out["gemm_tflops"] = g
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except (OSError, ValueError):
-            pass
-        peak = float(peaks.get("bf16_tflops", 1900.0))
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        dec = g[f"tcgen05_decoder_256x{s.D}x{K6}"]
-        # the decoder product reads its BF16 weights once (N K 2 bytes), the codes (M K 2) and writes
-        # the FP32 output (M N 4): 254 flop/byte at M = 256, below the bf16 ridge (~290), so HBM bounds it
-        dec_flop = 2.0 * 256 * s.D * K6
-        dec_bytes = 2.0 * s.D * K6 + 2.0 * 256 * K6 + 4.0 * 256 * s.D
-        dec_gbs = dec_bytes / (dec_flop / (dec * 1e12)) / 1e9
-        roof = {"bound": "hbm", "kernel": "gemm_tc_kernel (decoder product, 256 sources)",
-                "achieved": round(dec_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(dec_gbs / hbm, 4),
-                "traffic": None, "algorithmic_bytes": dec_bytes, "tflops": dec, "tensor_peak": peak,
-                "tensor_frac": round(dec / peak, 4), "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        roof = decoder_roofline(g[dec_name], SB, s.D, K6)
     s.close()
     m.close()
     del G
     torch.cuda.empty_cache()
     return out, roof
+
+
+def decoder_roofline(tflops, M, N, K):
+    """Roofline object of the decoder product C[M][N] = A[M][K] B[N][K]^T (BF16 in, FP32 out): it
+    reads its weights once (N K 2 bytes), the codes (M K 2) and writes the output (M N 4).  Below the
+    bf16 ridge (measured peak flop/s over measured HBM bytes/s) HBM bounds it, above it the tensor
+    cores do; the kernel is timed alone, so the burst bf16 peak applies."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    flop = 2.0 * M * N * K
+    nbytes = 2.0 * N * K + 2.0 * M * K + 4.0 * M * N
+    gbs = nbytes / (flop / (tflops * 1e12)) / 1e9
+    tensor = flop / nbytes > peak * 1e12 / (hbm * 1e9)
+    r = {"bound": "tensor" if tensor else "hbm", "kernel": f"gemm_tc_kernel (decoder product, {M} sources)",
+         "achieved": round(tflops if tensor else gbs, 1), "peak": peak if tensor else hbm,
+         "unit": "TFLOP/s" if tensor else "GB/s", "frac": round((tflops / peak) if tensor else (gbs / hbm), 4),
+         "traffic": None, "algorithmic_bytes": nbytes, "flop": flop, "flop_per_byte": round(flop / nbytes, 1),
+         "tflops": tflops, "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "tensor_frac": round(tflops / peak, 4),
+         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    return r
 
 
 def measure_surrogate(args):
