@@ -45,7 +45,11 @@
  *              clamped to 1; factor P = exp(-alpha dt / 2) applied before and
  *              after each split increment: s <- P (P s + dt c D).
  *   R-src      moment source: after the stress half of step n, each stress
- *              component at the source index gains M_ij w[n] (on its x split).
+ *              component at the source index gains M_ij w[n] (on its x split):
+ *              the stress-glut form of a moment tensor whose moment rate is
+ *              -(V / dt) M w(t - dt / 2), V = dx dy dz, in Aki & Richards'
+ *              sign convention (pinned against the analytic moment-tensor
+ *              solution in tests/test_oracle_moment.py).
  *              Force source: after the velocity half of step n, v_i at the
  *              source index gains dt f_i w[n] / (rho_stag dx dy dz).
  *   R-rec      sample n of a trace holds p(t_{n+1}) and v(t_{n+1/2}) at the

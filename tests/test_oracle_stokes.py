@@ -23,7 +23,10 @@ def _ricker_dot(t, f0, t0):
     return (2 * a - 3) * np.exp(-a) * 2 * s * np.pi * f0
 
 
-def stokes_velocity(i, j, xr, xs, t, rho, alpha, beta, f0, t0):
+def stokes_velocity(i, j, xr, xs, t, rho, alpha, beta, f0, t0, fdot=None):
+    """Component i of the velocity at xr from a force along x_j at xs; fdot(t) is the force
+    history's time derivative (default: the Ricker wavelet's, f0 and t0)."""
+    fd = fdot if fdot is not None else (lambda tt: _ricker_dot(tt, f0, t0))
     d = np.asarray(xr, float) - np.asarray(xs, float)
     r = np.linalg.norm(d)
     g = d / r
@@ -33,11 +36,10 @@ def stokes_velocity(i, j, xr, xs, t, rho, alpha, beta, f0, t0):
     xq, wq = np.polynomial.legendre.leggauss(400)
     lo, hi = r / alpha, r / beta
     tau = 0.5 * (hi - lo) * xq + 0.5 * (hi + lo)
-    near = (0.5 * (hi - lo)) * np.sum(wq[None, :] * tau[None, :] *
-                                      _ricker_dot(t[:, None] - tau[None, :], f0, t0), axis=1)
+    near = (0.5 * (hi - lo)) * np.sum(wq[None, :] * tau[None, :] * fd(t[:, None] - tau[None, :]), axis=1)
     v = (3 * gg - dij) / r ** 3 * near / (4 * np.pi * rho)
-    v += gg / (4 * np.pi * rho * alpha ** 2 * r) * _ricker_dot(t - r / alpha, f0, t0)
-    v -= (gg - dij) / (4 * np.pi * rho * beta ** 2 * r) * _ricker_dot(t - r / beta, f0, t0)
+    v += gg / (4 * np.pi * rho * alpha ** 2 * r) * fd(t - r / alpha)
+    v -= (gg - dij) / (4 * np.pi * rho * beta ** 2 * r) * fd(t - r / beta)
     return v
 
 
