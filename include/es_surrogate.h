@@ -99,6 +99,15 @@ int es_gemm_bf16(int M, int N, int K, const void* A, int lda, int a_t, const voi
  * mbarrier waits ran out since the last call (that launch's C is undefined). */
 int es_gemm_status(void);
 
+/* Test hook for the failure path of those waits (no fault, no hang): launches
+ * on `stream` one kernel in which a single thread waits, through the same
+ * bounded wait as the tcgen05 GEMM, on a barrier phase that nothing completes;
+ * after `seconds` of device time (0 < seconds <= 2) it gives up, sets the
+ * status word and returns, so the next es_gemm_status() reports
+ * ES_ERR_TIMEOUT and the context stays usable.  Returns ES_OK, ES_ERR_ARG
+ * (seconds out of range) or ES_ERR_CUDA. */
+int es_gemm_wait_probe(double seconds, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -357,6 +357,14 @@ int es_gemm_status(void)
     return v ? ES_ERR_TIMEOUT : ES_OK;
 }
 
+int es_gemm_wait_probe(double seconds, void* stream)
+{
+    if (!(seconds > 0.0) || seconds > 2.0) return ES_ERR_ARG;
+    cudaGetLastError();
+    CKS(gemm_wait_probe(seconds, static_cast<cudaStream_t>(stream)));
+    return ES_OK;
+}
+
 int es_gemm_bf16(int M, int N, int K, const void* A, int lda, int a_t, const void* B, int ldb, int b_nk, float* C,
                  int ldc, float alpha, float beta, int split_k, void* stream)
 {

@@ -63,7 +63,7 @@ static_assert(A_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "swizzle atoms mus
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 
-__device__ unsigned g_tc_status;  // bit 0 producer, 1 MMA, 2 epilogue, 3 MMA drain, 4 TMA drain gave up
+__device__ unsigned g_tc_status;  // bit 0 producer, 1 MMA, 2 epilogue, 3 MMA drain, 4 TMA drain, 5 probe gave up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -96,14 +96,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait for the phase of the given parity to complete
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// bounded wait for the phase of the given parity to complete: false after
+// limit_ns of global time
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = WAIT_NS)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned i = 1;; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if ((i & 63u) == 0 && global_ns() - t0 > WAIT_NS) return false;
+        if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// The timeout path of the bounded waits, on demand: one thread waits, through
+// mbar_wait, on the first phase of a fresh barrier that nothing arrives at,
+// gives up after limit_ns, records bit 5 of the status word and returns.
+__global__ void wait_probe_kernel(unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0, limit_ns)) atomicOr(&g_tc_status, 32u);
     }
 }
 
@@ -423,6 +437,13 @@ cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, c
     if (e != cudaSuccess) return e;
     gemm_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, nkb, kb_per, mt, ntl, (int)ntiles,
                                                                C, ldc, alpha, beta, split_k > 1 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_wait_probe(double seconds, cudaStream_t st)
+{
+    if (!(seconds > 0.0) || seconds > 2.0) return cudaErrorInvalidValue;
+    wait_probe_kernel<<<1, 32, 0, st>>>((unsigned long long)(seconds * 1e9));
     return cudaGetLastError();
 }
 

@@ -15,6 +15,9 @@ cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, c
                          float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st);
 // reads and clears the tcgen05 GEMM's device status word (bits set by waits that gave up)
 cudaError_t gemm_tc_status(unsigned* status);
+// Launches one kernel whose bounded wait on a barrier nothing completes gives
+// up after `seconds` (0 < seconds <= 2) and sets the status word.
+cudaError_t gemm_wait_probe(double seconds, cudaStream_t st);
 // out[c][r] = in[r][c] for a rows x cols BF16 matrix (row-major both)
 cudaError_t transpose_bf16(const __nv_bfloat16* in, long long rows, long long cols, __nv_bfloat16* out,
                            cudaStream_t st);

@@ -100,7 +100,7 @@ def exported_symbols():
             "es_kernels_per_step", "es_model_autotune", "es_fft_plan",
             "es_fft_plan_select", "es_sur_create", "es_sur_destroy", "es_sur_set_stream", "es_sur_num_params",
             "es_sur_get_params", "es_sur_set_params", "es_sur_set_output_scale", "es_sur_fit_output_scale",
-            "es_sur_predict", "es_sur_loss_grad", "es_sur_train_step", "es_sur_combine", "es_gemm_bf16", "es_gemm_status", "es_model_destroy", "es_status_string", "es_last_error"]
+            "es_sur_predict", "es_sur_loss_grad", "es_sur_train_step", "es_sur_combine", "es_gemm_bf16", "es_gemm_status", "es_gemm_wait_probe", "es_model_destroy", "es_status_string", "es_last_error"]
 
 
 def _check(status, where):

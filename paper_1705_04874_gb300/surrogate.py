@@ -52,6 +52,7 @@ def _lib():
             "es_sur_train_step": ([vp, vp, vp, vp, ci, cf, ctypes.POINTER(cf)], ci),
             "es_gemm_bf16": ([ci, ci, ci, vp, ci, ci, vp, ci, ci, vp, ci, cf, cf, ci, vp], ci),
             "es_gemm_status": ([], ci),
+            "es_gemm_wait_probe": ([ctypes.c_double, vp], ci),
             "es_sur_combine": ([vp, ci, ctypes.c_longlong, vp, vp, ci, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
@@ -78,6 +79,13 @@ def es_gemm_status():
     """Synchronizes the device; raises EsError if a bounded wait of the
     tcgen05 GEMM ran out since the last call (es_gemm_status)."""
     _check(_lib().es_gemm_status(), "es_gemm_status")
+
+
+def es_gemm_wait_probe(seconds, stream=None):
+    """Runs the bounded-wait failure path on the device (es_gemm_wait_probe):
+    one wait on a barrier nothing completes gives up after `seconds`; the next
+    es_gemm_status() raises EsError(ES_ERR_TIMEOUT)."""
+    _check(_lib().es_gemm_wait_probe(float(seconds), _es._stream_handle(stream)), "es_gemm_wait_probe")
 
 
 def es_gemm_bf16(A, B, C, a_t=False, b_nk=False, alpha=1.0, beta=0.0, split_k=1, stream=None):

@@ -60,3 +60,6 @@ def test_host_side_argument_checks(lib):
     assert lib.es_derivative(p, 600, 32, 32, 0, 1.0, 1, ctypes.c_void_p(a.ctypes.data + 4), None) == es.ES_ERR_SIZE
     assert lib.es_run(None, 10, 0.0, None, 0, None) == es.ES_ERR_ARG
     assert lib.es_kernels_per_step(None) == es.ES_ERR_ARG
+    lib.es_gemm_wait_probe.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    assert lib.es_gemm_wait_probe(0.0, None) == es.ES_ERR_ARG
+    assert lib.es_gemm_wait_probe(2.5, None) == es.ES_ERR_ARG

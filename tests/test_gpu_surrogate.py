@@ -78,6 +78,30 @@ def test_tcgen05_gemm_k_major(env, M, N, K, split, beta):
     assert np.array_equal(got[:, N:], C0[:, N:])  # columns past N untouched
 
 
+def test_bounded_wait_times_out_and_the_context_survives(env):
+    """The failure path of the tcgen05 GEMM's bounded waits, without a fault
+    or a hang: a wait on a barrier phase that nothing completes gives up after
+    50 ms, the status word reports ES_ERR_TIMEOUT once and is cleared, and the
+    same context then runs a tcgen05 GEMM correctly."""
+    import time
+    es, sur, torch = env
+    sur.es_gemm_status()  # starts clear
+    t0 = time.perf_counter()
+    sur.es_gemm_wait_probe(0.05)
+    with pytest.raises(es.EsError) as err:
+        sur.es_gemm_status()
+    assert err.value.status == es.ES_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.05
+    sur.es_gemm_status()  # read once, then clear
+    rng = np.random.default_rng(1)
+    A, B = _bf(torch, rng.standard_normal((136, 200))), _bf(torch, rng.standard_normal((264, 200)))
+    C = torch.zeros((136, 264), device="cuda")
+    sur.es_gemm_bf16(A, B, C, b_nk=True)
+    sur.es_gemm_status()
+    ref = A.float().cpu().numpy().astype(np.float64) @ B.float().cpu().numpy().astype(np.float64).T
+    assert np.abs(C.cpu().numpy() - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
 def test_loss_and_gradients_match_oracle(env):
     es, sur, torch = env
     from oracle import surrogate as osur
