@@ -78,8 +78,8 @@ int ensure_wdt(es_sur* s)
 
 // forward through the decoder on the tcgen05 tensor cores (both operands
 // K-major: z [B][6K] and WdT [D][6K]): s->U = z Wd in normalized units, or for
-// inference (out != nullptr) one call per output component writing
-// out[:, c D/4 ...] directly with that component's scale as alpha.
+// inference (out != nullptr) one product writing out directly, the columns of
+// component c scaled by that component's RMS.
 int forward(es_sur* s, const float* pos, const float* mt, int B, float* out = nullptr)
 {
     int rc = ensure_wdt(s);
@@ -96,10 +96,9 @@ int forward(es_sur* s, const float* pos, const float* mt, int B, float* out = nu
     CKS(sur_bias_act(s->A, s->p + s->ob3, B, s->K, false, nullptr, s->st));
     CKS(sur_outer(mt, s->A, B, s->K, s->Zb, s->st));
     if (out) {
-        const long long Dc = s->D / 4;
-        for (int c = 0; c < 4; ++c)
-            CKS(gemm_bf16(B, (int)Dc, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT + (size_t)c * Dc * 6 * s->K, 6 * s->K,
-                          true, out + (size_t)c * Dc, (int)s->D, s->scale_h[c], 0.f, 1, s->st));
+        // one product over all four components, each column block scaled by its component's RMS
+        CKS(gemm_bf16_tc(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, s->WdT, 6 * s->K, out, (int)s->D, 1.f, 0.f, 1, s->st,
+                         s->scale_h, (int)(s->D / 4)));
     } else
         CKS(gemm_bf16(B, (int)s->D, 6 * s->K, s->Zb, 6 * s->K, false, s->WdT, 6 * s->K, true, s->U, (int)s->D, 1.f,
                       0.f, 1, s->st));

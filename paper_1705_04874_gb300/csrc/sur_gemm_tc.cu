@@ -181,7 +181,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                    int nkb, int kb_per, int mt, int ntl, int ntiles, float* __restrict__ C, int ldc, float alpha,
-                   float beta, int atomic)
+                   float beta, int atomic, float4 alpha4, int span)
 {
     extern __shared__ uint8_t dyn[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], mma_done;
@@ -306,10 +306,24 @@ __global__ void __launch_bounds__(THREADS, 1)
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TN + c0), r);
                 float4* srow = reinterpret_cast<float4*>(stage + lane * EPI_LD);
+                if (span) {
+                    // per-column alpha: columns [c span, (c + 1) span) of C take component c of alpha4
+                    float a[32];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    srow[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
-                                          alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        a[j] = (col < span ? alpha4.x : col < 2 * span ? alpha4.y : col < 3 * span ? alpha4.z
+                                                                                                  : alpha4.w) *
+                               __uint_as_float(r[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) srow[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        srow[j] = make_float4(alpha * __uint_as_float(r[4 * j]), alpha * __uint_as_float(r[4 * j + 1]),
+                                              alpha * __uint_as_float(r[4 * j + 2]), alpha * __uint_as_float(r[4 * j + 3]));
+                }
                 __syncwarp();
                 // lane l stores columns 4 (l mod 8) .. +3 of row 4 i + l / 8: a warp instruction writes
                 // four whole 128-byte row segments
@@ -406,8 +420,11 @@ bool make_map(EncodeTiled fn, CUtensorMap* map, const __nv_bfloat16* ptr, int ro
 }  // namespace
 
 cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st)
+                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st,
+                         const float* alpha4, int span)
 {
+    if (alpha4 && (span < 1 || (long long)4 * span < N)) return cudaErrorInvalidValue;
+    const float4 av = alpha4 ? make_float4(alpha4[0], alpha4[1], alpha4[2], alpha4[3]) : make_float4(0.f, 0.f, 0.f, 0.f);
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
     if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N) return cudaErrorInvalidValue;
@@ -436,7 +453,8 @@ cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, c
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     gemm_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mapA, mapB, M, N, nkb, kb_per, mt, ntl, (int)ntiles,
-                                                               C, ldc, alpha, beta, split_k > 1 ? 1 : 0);
+                                                               C, ldc, alpha, beta, split_k > 1 ? 1 : 0, av,
+                                                               alpha4 ? span : 0);
     return cudaGetLastError();
 }
 

@@ -10,9 +10,12 @@ namespace es {
 cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, bool a_t, const __nv_bfloat16* B,
                       int ldb, bool b_nk, float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st);
 
-// the K-major case (A [M][K], B [N][K]) on tcgen05 tensor cores; see sur_gemm_tc.cu
+// the K-major case (A [M][K], B [N][K]) on tcgen05 tensor cores; see sur_gemm_tc.cu.
+// alpha4 (host, 4 values) with span > 0: column n of C takes alpha4[n / span] instead of
+// alpha (4 span >= N), e.g. one scale per output component of the decoder
 cudaError_t gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st);
+                         float* C, int ldc, float alpha, float beta, int split_k, cudaStream_t st,
+                         const float* alpha4 = nullptr, int span = 0);
 // reads and clears the tcgen05 GEMM's device status word (bits set by waits that gave up)
 cudaError_t gemm_tc_status(unsigned* status);
 // Launches one kernel whose bounded wait on a barrier nothing completes gives
