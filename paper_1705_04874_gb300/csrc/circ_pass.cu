@@ -320,7 +320,6 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
 
 }  // namespace
 
-size_t circ_smem_bytes(int n) { return circ_smem(n, false, true); }
 
 cudaError_t prepare_circ_kernels()
 {

@@ -69,7 +69,6 @@ cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
 constexpr int CIRC_MAX_N = 512;
 cudaError_t launch_circ(const PassParams& p, cudaStream_t st);
 cudaError_t prepare_circ_kernels();
-size_t circ_smem_bytes(int n);
 // Opts every pass kernel into the shared memory it needs (once per device).
 cudaError_t prepare_pass_kernels();
 

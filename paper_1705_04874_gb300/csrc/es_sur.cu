@@ -238,7 +238,7 @@ int es_sur_set_stream(es_sur* s, void* stream)
     return ES_OK;
 }
 
-long long es_sur_num_params(const es_sur* s) { return s ? (long long)s->P : ES_ERR_ARG; }
+long long es_sur_num_params(const es_sur* s) { return s ? (long long)s->P : (long long)ES_ERR_ARG; }
 
 int es_sur_get_params(es_sur* s, float* params)
 {
