@@ -1,5 +1,7 @@
 """Parity at the benchmark's full grid sizes, in the launch configuration the
-benchmark times (es_run through the C ABI): 128^3 and 256^3 marine models.
+benchmark times (es_run and es_run_group through the C ABI): 128^3 and 256^3
+marine models, and the batched group of 64 + 16 + 8 sources on 128^3, 96^3
+and 160^3.
 The oracle cannot run thousands of steps at these sizes in a test, so the
 whole field state is compared after a few steps, and properties that hold at
 any length (exact linearity and delay, receiver maps, energy conservation with
@@ -8,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_1705_04874_gb300 import synth
-from conftest import cfl_dt, rel_l2
+from conftest import cfl_dt, rel_l2, trace_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -121,3 +123,46 @@ def test_energy_conserved_without_pml_128(es, orc):
     es_ = np.array(es_)
     assert es_.min() > 0
     assert (es_.max() - es_.min()) / es_.max() < 2e-4, es_
+
+
+def test_batched_group_full_size(es, orc):
+    """The batched workload as the benchmark runs it: 64 sources on the 128^3
+    marine model, 16 on 96^3 and 8 on 160^3 (random double couples in the
+    reservoir boxes, Ricker 30 Hz), 32 x 32 seabed receivers each, all in one
+    graph through es_run_group, 200 steps.  Sampled simulations of every model
+    equal single-source runs bit for bit (same kernels, same arithmetic), and
+    the first simulation on 96^3 matches the oracle over all 200 samples."""
+    nt = 200
+    specs = [(128, 10, 64), (96, 8, 16), (160, 10, 8)]
+    models, rcvs, dts, inputs = [], [], [], []
+    try:
+        for i, (n, pml, nb) in enumerate(specs):
+            rho, cp, cs = synth.marine_model(n, seed=1)
+            dt = 0.3 * 10.0 / float(cp.max())
+            rng = synth.SplitMix64(40 + i)
+            box = synth.reservoir_box((n, n, n), pml)
+            pos = synth.random_positions(rng, box, nb)
+            mts = np.array([synth.random_dc(rng) for _ in range(nb)])
+            wav = np.stack([synth.ricker(nt, dt, 30.0)] * nb)
+            m = es.Model(rho, cp, cs, dx=10.0, pml=pml)
+            rcv = m.seabed_receivers(32, 32)
+            m.batch_set(pos, mts, wav)
+            models.append(m)
+            rcvs.append(rcv)
+            dts.append(dt)
+            inputs.append((rho, cp, cs, pml, pos, mts, wav))
+        got = es.es_run_group(models, nt, dts, rcvs)
+    finally:
+        for m in models:
+            m.close()
+    for i, b in [(0, 0), (0, 63), (1, 15), (2, 7)]:
+        rho, cp, cs, pml, pos, mts, wav = inputs[i]
+        with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m1:
+            m1.source_set(pos[b], mts[b], wav[b])
+            single = m1.run(nt, dts[i], rcvs[i])
+        assert np.array_equal(got[i][b], single), (i, b)
+    rho, cp, cs, pml, pos, mts, wav = inputs[1]
+    ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dts[1], nt=nt, pml=pml,
+                       sources=[dict(kind="moment", pos=pos[0], m=mts[0], w=wav[0])], receivers=rcvs[1])["traces"]
+    err = trace_errors(got[1][0], ref)
+    assert np.median(err) < 1e-4 and err.max() < 1e-3, (np.median(err), err.max())
