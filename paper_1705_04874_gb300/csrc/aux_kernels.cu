@@ -94,6 +94,60 @@ cudaError_t launch_visc_combine(float* const* fields, float* vold, float* w, siz
     return cudaGetLastError();
 }
 
+// Material coefficients of one cell per thread (Eq. (4) and the staggered
+// averages of the model setup): lambda = rho cp^2 - 2 mu and mu = rho cs^2 at
+// the cell, buoyancy 2 / (rho_i + rho_(i+1)) at the half-index point along
+// each axis, and the edge shear moduli as the harmonic mean of the four
+// surrounding mu (0 if any is 0, i.e. next to water); neighbours wrap
+// periodically.  FP64 with explicitly rounded operations (no contraction),
+// stored in FP32.
+__device__ __forceinline__ double mu_of(const float* rho, const float* cs, size_t p)
+{
+    const double s = cs[p];
+    return __dmul_rn(__dmul_rn(s, s), (double)rho[p]);
+}
+
+__device__ __forceinline__ double harmonic4(double a, double b, double c, double d)
+{
+    if (a == 0.0 || b == 0.0 || c == 0.0 || d == 0.0) return 0.0;
+    const double s = __dadd_rn(__dadd_rn(__dadd_rn(__ddiv_rn(1.0, a), __ddiv_rn(1.0, b)), __ddiv_rn(1.0, c)),
+                               __ddiv_rn(1.0, d));
+    return __ddiv_rn(4.0, s);
+}
+
+__global__ void materials_kernel(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz,
+                                 MatPtrs out)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((size_t)nx * ny));
+        const int ip = i + 1 == nx ? 0 : i + 1, jp = j + 1 == ny ? 0 : j + 1, kp = k + 1 == nz ? 0 : k + 1;
+        auto at = [&](int ii, int jj, int kk) { return (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * kk); };
+        const size_t qx = at(ip, j, k), qy = at(i, jp, k), qz = at(i, j, kp);
+        const double r = rho[q], c = cp[q];
+        const double mu = mu_of(rho, cs, q);
+        out.p[M_LAM][q] = __double2float_rn(__dsub_rn(__dmul_rn(__dmul_rn(c, c), r), __dmul_rn(2.0, mu)));
+        out.p[M_MU][q] = __double2float_rn(mu);
+        out.p[M_BX][q] = __double2float_rn(__ddiv_rn(2.0, __dadd_rn(r, (double)rho[qx])));
+        out.p[M_BY][q] = __double2float_rn(__ddiv_rn(2.0, __dadd_rn(r, (double)rho[qy])));
+        out.p[M_BZ][q] = __double2float_rn(__ddiv_rn(2.0, __dadd_rn(r, (double)rho[qz])));
+        const double mx = mu_of(rho, cs, qx), my = mu_of(rho, cs, qy), mz = mu_of(rho, cs, qz);
+        out.p[M_MUXY][q] = __double2float_rn(harmonic4(mu, mx, my, mu_of(rho, cs, at(ip, jp, k))));
+        out.p[M_MUXZ][q] = __double2float_rn(harmonic4(mu, mx, mz, mu_of(rho, cs, at(ip, j, kp))));
+        out.p[M_MUYZ][q] = __double2float_rn(harmonic4(mu, my, mz, mu_of(rho, cs, at(i, jp, kp))));
+    }
+}
+
+cudaError_t launch_materials(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz,
+                             const MatPtrs& out, cudaStream_t st)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 32);
+    materials_kernel<<<(unsigned)blocks, 256, 0, st>>>(rho, cp, cs, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
 __global__ void fill_kernel(float* p, size_t n, float v)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;

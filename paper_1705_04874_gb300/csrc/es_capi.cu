@@ -71,8 +71,8 @@ int fetch(const T* src, size_t n, std::vector<T>& out, cudaStream_t st)
 }
 
 // Runs f(lo, hi) over [0, n) split into contiguous blocks of at least `grain`
-// items on the host's cores (model setup: per-cell FP64 material math, no
-// shared writes between blocks).
+// items on the host's cores (model setup: the input checks; no shared writes
+// between blocks).
 template <class F>
 void parallel_for(size_t n, F f, size_t grain = 1)
 {
@@ -722,43 +722,26 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     m->d_int = (int*)take(16);
     m->d_fields = (float**)take(NFIELD * sizeof(float*));
 
-    // materials in FP64 (Eq. (4) and the staggered averages), stored in FP32
+    // materials (Eq. (4) and the staggered averages) on the device, from rho, cp, cs there: the
+    // caller's device arrays as they are, host arrays through one staging buffer
     {
-        std::vector<float> h(n);
-        auto idx = [&](int i, int j, int k) { return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k); };
-        std::vector<double> mu(n), lam(n);
-        parallel_for(n, [&](size_t q0, size_t q1) {
-            for (size_t q = q0; q < q1; ++q) {
-                mu[q] = (double)h_cs[q] * h_cs[q] * h_rho[q];
-                lam[q] = (double)h_cp[q] * h_cp[q] * h_rho[q] - 2.0 * mu[q];
-            }
-        }, 65536);
-        auto hmean = [](double a, double b, double c, double d) {
-            return (a == 0.0 || b == 0.0 || c == 0.0 || d == 0.0) ? 0.0 : 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d);
-        };
-        for (int which = 0; which < NMAT && e == cudaSuccess; ++which) {
-            parallel_for((size_t)nz, [&](size_t k0, size_t k1) {
-            for (int k = (int)k0; k < (int)k1; ++k)
-                for (int j = 0; j < ny; ++j)
-                    for (int i = 0; i < nx; ++i) {
-                        const size_t q = idx(i, j, k);
-                        const size_t qx = idx((i + 1) % nx, j, k), qy = idx(i, (j + 1) % ny, k), qz = idx(i, j, (k + 1) % nz);
-                        double v = 0.0;
-                        switch (which) {
-                        case M_BX: v = 2.0 / ((double)h_rho[q] + h_rho[qx]); break;
-                        case M_BY: v = 2.0 / ((double)h_rho[q] + h_rho[qy]); break;
-                        case M_BZ: v = 2.0 / ((double)h_rho[q] + h_rho[qz]); break;
-                        case M_LAM: v = lam[q]; break;
-                        case M_MU: v = mu[q]; break;
-                        case M_MUXY: v = hmean(mu[q], mu[qx], mu[qy], mu[idx((i + 1) % nx, (j + 1) % ny, k)]); break;
-                        case M_MUXZ: v = hmean(mu[q], mu[qx], mu[qz], mu[idx((i + 1) % nx, j, (k + 1) % nz)]); break;
-                        case M_MUYZ: v = hmean(mu[q], mu[qy], mu[qz], mu[idx(i, (j + 1) % ny, (k + 1) % nz)]); break;
-                        }
-                        h[q] = (float)v;
-                    }
-            });
-            e = cudaMemcpy(m->mat[which], h.data(), n * 4, cudaMemcpyHostToDevice);
+        const bool on_dev = is_device_ptr(rho) && is_device_ptr(cp) && is_device_ptr(cs);
+        float* stage = nullptr;
+        const float *d_rho = rho, *d_cp = cp, *d_cs = cs;
+        if (!on_dev) {
+            e = cudaMalloc(&stage, 3 * n * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemcpy(stage, h_rho.data(), n * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(stage + n, h_cp.data(), n * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(stage + 2 * n, h_cs.data(), n * 4, cudaMemcpyHostToDevice);
+            d_rho = stage;
+            d_cp = stage + n;
+            d_cs = stage + 2 * n;
         }
+        MatPtrs mp;
+        for (int k = 0; k < NMAT; ++k) mp.p[k] = m->mat[k];
+        if (e == cudaSuccess) e = launch_materials(d_rho, d_cp, d_cs, nx, ny, nz, mp, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (stage) cudaFree(stage);
     }
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = upload_axis_tables(m, a);
     for (int k = 0; k < 2 * KPS_MAX && e == cudaSuccess; ++k) e = cudaEventCreate(&m->ev[k]);

@@ -93,6 +93,12 @@ cudaError_t launch_transpose_traces(const float* rec, int nt, int cols, float* o
 cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* ev_src,
                              const float* ev_amp, const int* ev_shift, int n_events, int n_out,
                              float* gather, cudaStream_t st);
+struct MatPtrs {
+    float* p[NMAT];  // the material arrays, indexed by M_BX ... M_MUYZ
+};
+// model setup on the device: every material array from rho, cp, cs (device, [nz][ny][nx])
+cudaError_t launch_materials(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz,
+                             const MatPtrs& out, cudaStream_t st);
 cudaError_t launch_fill(float* p, size_t n, float v, cudaStream_t st);
 cudaError_t launch_visc_combine(float* const* fields, float* vold, float* w, size_t n, float a, float b,
                                 cudaStream_t st);
