@@ -63,3 +63,27 @@ def test_host_side_argument_checks(lib):
     lib.es_gemm_wait_probe.argtypes = [ctypes.c_double, ctypes.c_void_p]
     assert lib.es_gemm_wait_probe(0.0, None) == es.ES_ERR_ARG
     assert lib.es_gemm_wait_probe(2.5, None) == es.ES_ERR_ARG
+
+
+def test_surrogate_host_side_argument_checks(lib):
+    """Bad network shapes and GEMM arguments are rejected before any device work."""
+    from paper_1705_04874_gb300 import es
+    from paper_1705_04874_gb300.surrogate import Config
+    h = ctypes.c_void_p()
+    lib.es_sur_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.es_sur_create(None, ctypes.byref(h)) == es.ES_ERR_ARG
+    good = dict(nfreq=3, hidden=64, latent=16, n_rcv=4, nt=16, max_batch=32, seed=1)
+    for field, bad in [("nfreq", 17), ("nfreq", -1), ("hidden", 12), ("latent", 4), ("n_rcv", 0), ("nt", 12),
+                       ("max_batch", 4), ("max_batch", 20)]:
+        cfg = Config(**{**good, field: bad})
+        assert lib.es_sur_create(ctypes.byref(cfg), ctypes.byref(h)) == es.ES_ERR_ARG, (field, bad)
+        assert not h.value
+    lib.es_gemm_bf16.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                      ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                      ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_void_p]
+    a = np.zeros(64, np.float32)
+    p = ctypes.c_void_p(a.ctypes.data)
+    assert lib.es_gemm_bf16(8, 8, 8, None, 8, 0, p, 8, 1, p, 8, 1.0, 0.0, 1, None) == es.ES_ERR_ARG
+    assert lib.es_gemm_bf16(8, 8, 12, p, 16, 0, p, 16, 1, p, 8, 1.0, 0.0, 1, None) == es.ES_ERR_ARG  # K % 8
+    assert lib.es_gemm_bf16(8, 8, 8, p, 4, 0, p, 8, 1, p, 8, 1.0, 0.0, 1, None) == es.ES_ERR_ARG  # lda < K
+    assert lib.es_sur_num_params(None) == es.ES_ERR_ARG
