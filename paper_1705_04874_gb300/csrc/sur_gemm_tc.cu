@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int mi = t % mt, ni = (t / mt) % ntl;
             const int b = lt & 1;
-            // one lane waits and the warp follows its verdict: tcgen05.ld below needs the whole warp
+            // one lane waits and the warp follows its result: tcgen05.ld below needs the whole warp
             int got = 0;
             if (lane == 0) got = mbar_wait(&acc_full[b], (lt >> 1) & 1) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
