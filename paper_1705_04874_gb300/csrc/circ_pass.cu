@@ -286,8 +286,11 @@ __global__ void __launch_bounds__(CTHREADS, 2) circ_x(const __grid_constant__ Pa
     if (COMP) load_kernel_row(cl, J.sign > 0 ? p.ckp_lo : p.ckm_lo, n, tid);
     // the tile's lines are one contiguous block of nl * n floats
     const float* src = J.src + off + (size_t)line0 * n;
-    for (int e = tid; e < np * ROW; e += blockDim.x) tile[e] = 0.f;  // rows and lines past the edges
-    __syncthreads();
+    // zeros where no copy lands (rows past the axis end; lines past the last tile's end), written
+    // alongside the copies, which touch only the other elements
+    for (int e = tid; e < (np - n) * ROW; e += blockDim.x) tile[n * ROW + e] = 0.f;
+    if (nl < TP)
+        for (int e = tid; e < n * (TP - nl); e += blockDim.x) tile[(e / (TP - nl)) * ROW + nl + e % (TP - nl)] = 0.f;
     // element e = r n + pos of the block; (r, pos) advance by blockDim.x without a division per element
     const int bd = blockDim.x, dr = bd / n, dp = bd % n;
     for (int r = tid / n, pos = tid % n; r < nl;) {
