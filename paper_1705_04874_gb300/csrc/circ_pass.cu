@@ -33,7 +33,7 @@
 // (registers), 10 FP32 operations per multiply-add.
 #include <cstdlib>
 
-#include "fft_pass.cuh"
+#include "circ_epilogue.cuh"
 
 namespace es {
 namespace {
@@ -85,38 +85,6 @@ __host__ __device__ inline int circ_row_len(int n) { return 2 * circ_pad(n) + 2 
 __host__ __device__ inline size_t circ_smem(int n, bool comp, bool two_tiles)
 {
     return sizeof(float) * ((two_tiles ? 2 : 1) * (size_t)circ_pad(n) * ROW + (comp ? 2 : 1) * (size_t)circ_row_len(n));
-}
-
-// scalar epilogue for one cell (same arithmetic as epilogue_pair)
-__device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos, int x, int y,
-                                             int z, float d, size_t off, size_t soff)
-{
-    if (J.kind == JOB_STORE) {
-        J.tgt[0][off + q] = d;
-        return;
-    }
-    const float dt = p.dt;
-    const bool slab = in_slab(pos, p.n, p.L);
-    const int S = 2 * p.L + 1;
-    if (J.kind == JOB_SINGLE) {
-        float inc = dt * __ldg(J.coef[0] + q) * d;
-        if (slab) {
-            const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
-            const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
-            inc = split_delta(J.slab[0], soff + si, P, inc);
-        }
-        atomicAdd(J.tgt[0] + off + q, inc);
-    } else {
-        const float lam = __ldg(J.coef[0] + q), mu = __ldg(J.coef[1] + q);
-        const float P = slab ? __ldg(p.pc + pos) : 1.f;
-        const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            float inc = dt * (lam + (t == J.diag ? 2.f * mu : 0.f)) * d;
-            if (slab) inc = split_delta(J.slab[t], soff + si, P, inc);
-            atomicAdd(J.tgt[t] + off + q, inc);
-        }
-    }
 }
 
 // out[i][lane] = sum_j c[(i - j) mod n] tile[j][lane] for i < n; rows j >= n
@@ -196,11 +164,10 @@ __device__ __forceinline__ void load_kernel_row(float* cw, const float* c, int n
     }
 }
 
-// Long axes (n >= CIRC_DIRECT_N) give every warp several 16-output chunks: the y and z
-// passes then run the epilogue straight from the registers (no output tile, half the
-// shared memory, twice the resident CTAs); shorter axes keep the output tile so that all
-// eight warps share the epilogue.
-constexpr int CIRC_DIRECT_N = 192;
+// Long axes (n >= CIRC_DIRECT_N, es_internal.h) give every warp several 16-output chunks:
+// the y and z passes then run the epilogue straight from the registers (no output tile,
+// half the shared memory, twice the resident CTAs); shorter axes keep the output tile so
+// that all warps share the epilogue.
 
 // y and z passes: blockIdx.x = (tile of 32 consecutive x) x outer x simulation, blockIdx.y = job
 template <bool COMP, bool DIRECT>
@@ -342,6 +309,7 @@ cudaError_t prepare_circ_kernels()
 
 cudaError_t launch_circ(const PassParams& p, cudaStream_t st)
 {
+    if (circ_tc_eligible(p)) return launch_circ_tc(p, st);
     if (p.n < 2 || p.n > CIRC_MAX_N || !p.ckp || !p.ckm) return cudaErrorInvalidValue;
     if (p.comp && (!p.ckp_lo || !p.ckm_lo)) return cudaErrorInvalidValue;
     const int threads = 32 * circ_warps(circ_pad(p.n) / (p.comp ? 8 : OB));

@@ -1,0 +1,368 @@
+// Circulant derivative passes on the fifth-generation tensor cores, for long
+// z axes without an FFT plan (n from CIRC_DIRECT_N to 512, FP32 mode; the
+// paper's 301-cell axis).  Along the axis the staggered derivative is the
+// dense contraction out[o][p] = sum_i C[o][i] f[i][p] (circulant C, pencils
+// p), so it runs as a tcgen05 GEMM whose A operand is a tile of 128 pencils
+// (the field, K = inputs) and whose B operand is the kernel matrix (N =
+// outputs, K = inputs).
+//
+// FP32 accuracy from BF16 products: each field value is split exactly into
+// three BF16 parts (f = f0 + f1 + f2, computed in FP32 by the converter
+// warps), each kernel value into three BF16 parts on the host (c = c0 + c1 +
+// c2 to about 2^-24), and the six products with split orders summing to at
+// most 2 are accumulated in FP32 in tensor memory; the three dropped products
+// are below 2^-24 of the result, the size of FP32 rounding.
+//
+// One CTA per tile of 128 pencils and one job, 6 warps:
+//   warp 0, one thread: TMA producer of the kernel-matrix splits, in chunks
+//       of up to 256 outputs x 64 inputs, through a 3-stage ring;
+//   warp 1: allocates tensor memory; one thread issues tcgen05.mma (M 128,
+//       N 256 or 64, K 16) into the accumulator (columns = outputs);
+//   warps 2-5: converters -- per k-block of 64 inputs they load the field
+//       block (coalesced along the pencils), split it, and write the three
+//       128 x 64 BF16 tiles in the 128-byte-swizzled K-major layout the MMA
+//       reads (double-buffered); then the epilogue: tensor-memory lane =
+//       pencil, so each tcgen05.ld gives a thread 32 consecutive outputs of
+//       its pencil, and a warp stores 32 consecutive cells of the derivative
+//       per instruction into a scratch array (plain stores: nothing to wait
+//       for).  The field update with its PML splits then runs as a separate
+//       element-wise kernel at full occupancy (circ_tc_update_kernel): done
+//       here by the four epilogue warps of one CTA per SM, its dependent
+//       coefficient loads made the pass latency-bound.
+// Every mbarrier wait is bounded; a wait that runs out records a status bit
+// (circ_tc_status) and the CTA finishes.
+#include <algorithm>
+
+#include "es_internal.h"
+#include "circ_epilogue.cuh"
+#include "tc_ptx.cuh"
+
+namespace es {
+namespace {
+
+using namespace tcx;
+
+constexpr int CT_P = 128;                   // pencils per tile (MMA M, tensor-memory lanes)
+constexpr int CT_K = 64;                    // inputs per k-block (one 128-byte swizzle row of BF16)
+constexpr int CT_OC = 256;                  // outputs per MMA chunk (MMA N)
+constexpr int CT_A_SPLIT = CT_P * CT_K * 2;  // 16 KB: one split of a field block
+constexpr int CT_A_BUF = 3 * CT_A_SPLIT;    // 48 KB per k-block
+constexpr int CT_B_STAGE = CT_OC * CT_K * 2;  // 32 KB: one split of one output chunk
+constexpr int CT_B_STAGES = 3;
+constexpr int CT_SMEM = 2 * CT_A_BUF + CT_B_STAGES * CT_B_STAGE + 1024;
+constexpr int CT_THREADS = 192;
+constexpr int CT_CONV = 128;                // converter / epilogue threads (warps 2-5)
+
+__device__ unsigned g_ctc_status;  // bit 0 producer, 1 MMA, 2 converter, 3 epilogue, 4 drain gave up
+
+struct CircMaps {
+    CUtensorMap m[6];  // kernel-matrix splits: [sign D+ / D-][split 0..2], rows = outputs, K = inputs
+};
+
+// instruction descriptor for kind::f16, D FP32, A and B BF16, both K-major, M 128, N = n
+__device__ __forceinline__ uint32_t ct_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(CT_P >> 4) << 24);
+}
+
+// byte offset of element (row r, k) in a 128-byte-swizzled K-major BF16 tile (64 per row)
+__device__ __forceinline__ uint32_t sw128_off(int r, int k)
+{
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_constant__ PassParams p,
+                                                                const __grid_constant__ CircMaps maps)
+{
+    extern __shared__ uint8_t dyn[];
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[CT_B_STAGES], b_empty[CT_B_STAGES], acc_full;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_issued, s_consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (smem_u32(dyn) + 1023u) & ~1023u;
+    uint8_t* gbase = dyn + (base - smem_u32(dyn));  // generic pointer to the aligned base
+    const uint32_t a_base = base, b_base = base + 2 * CT_A_BUF;
+
+    const int n = p.n, nkb = (n + CT_K - 1) / CT_K;
+    const int nop = (n + 63) / 64 * 64;                 // outputs padded to whole 64-row boxes
+    const int noc = (nop + CT_OC - 1) / CT_OC;         // output chunks
+    const long long P = (long long)p.nx * p.ny;        // pencils of the z pass (x + nx y)
+    const int ntile = (int)((P + CT_P - 1) / CT_P);
+    const int u = blockIdx.x;
+    const int job = u / (p.nsim * ntile), rr = u % (p.nsim * ntile);
+    const int sim = rr % p.nsim, tile = rr / p.nsim;
+    const long long p0 = (long long)tile * CT_P;
+    const PassJob& J = p.job[job];
+    const size_t est = (size_t)p.nx * p.ny;
+    const size_t off = (size_t)sim * p.fstride;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], CT_CONV);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int s = 0; s < CT_B_STAGES; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    __syncwarp();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    pdl_begin(p.pdl);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // kernel-matrix splits: for every k-block, split and output chunk in the MMA's order
+            const int mb = J.sign > 0 ? 0 : 3;
+            int it = 0;
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; ++kb)
+                for (int sb = 0; sb < 3 && ok; ++sb)
+                    for (int oc = 0; oc < noc; ++oc, ++it) {
+                        const int s = it % CT_B_STAGES;
+                        if (!mbar_wait(&b_empty[s], ((it / CT_B_STAGES) & 1) ^ 1)) {
+                            atomicOr(&g_ctc_status, 1u);
+                            ok = false;
+                            break;
+                        }
+                        const int rows = min(CT_OC, nop - oc * CT_OC);  // a multiple of 64
+                        mbar_expect_tx(&b_full[s], (unsigned)rows * 128u);
+                        for (int bx = 0; bx < rows / 64; ++bx)
+                            tma_load_2d(b_base + s * CT_B_STAGE + bx * 8192, &maps.m[mb + sb], &b_full[s], kb * CT_K,
+                                        oc * CT_OC + bx * 64);
+                    }
+            s_issued = it;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int a = kb & 1;
+                if (!mbar_wait(&a_full[a], (kb >> 1) & 1)) {
+                    atomicOr(&g_ctc_status, 2u);
+                    break;
+                }
+                tc_fence_after();
+                for (int sb = 0; sb < 3 && ok; ++sb)
+                    for (int oc = 0; oc < noc; ++oc, ++it) {
+                        const int s = it % CT_B_STAGES;
+                        if (!mbar_wait(&b_full[s], (it / CT_B_STAGES) & 1)) {
+                            atomicOr(&g_ctc_status, 2u);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int rows = min(CT_OC, nop - oc * CT_OC);
+                        const uint32_t idesc = ct_idesc(rows);
+                        const uint64_t db = sw128_desc(b_base + s * CT_B_STAGE);
+                        // field splits sa with sa + sb <= 2
+                        for (int sa = 0; sa + sb <= 2; ++sa) {
+                            const uint64_t da = sw128_desc(a_base + a * CT_A_BUF + sa * CT_A_SPLIT);
+#pragma unroll
+                            for (int k = 0; k < CT_K / 16; ++k) {
+                                const uint64_t step = (uint64_t)((k * 32) >> 4);
+                                const bool first = kb == 0 && sb == 0 && sa == 0 && k == 0;
+                                tc_mma(tmem + (uint32_t)(oc * CT_OC), da + step, db + step, idesc, first ? 0u : 1u);
+                            }
+                        }
+                        tc_commit(&b_empty[s]);
+                    }
+                if (ok) tc_commit(&a_empty[a]);
+            }
+            s_consumed = it;
+            if (ok) tc_commit(&acc_full);
+        }
+    } else {
+        // converters: field block (64 inputs x 128 pencils) -> three BF16 tiles [pencil][input]
+        const int t = threadIdx.x - 64;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int a = kb & 1;
+            // one thread waits until the MMAs have released the buffer, the others follow at a named
+            // barrier of the converter warps; a wait that runs out (after another role gave up) is
+            // recorded and the block is written anyway (the results are then void, nothing hangs)
+            if (t == 0 && !mbar_wait(&a_empty[a], ((kb >> 1) & 1) ^ 1)) atomicOr(&g_ctc_status, 4u);
+            asm volatile("bar.sync 1, %0;" ::"r"(CT_CONV) : "memory");
+            uint8_t* abuf = gbase + a * CT_A_BUF;
+            // thread t owns pencil t of the tile: 16 loads in flight (coalesced over the threads),
+            // then each group of 8 consecutive inputs goes out as one 16-byte store per split (one
+            // swizzle chunk; the 8 rows of a quarter-warp hit 8 distinct bank groups)
+            const long long pg = p0 + t;
+            const bool pv = pg < P;
+            const float* col = J.src + off + (size_t)(pv ? pg : 0);
+#pragma unroll 1
+            for (int c2 = 0; c2 < CT_K / 8; c2 += 2) {
+                float xv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int gi = kb * CT_K + c2 * 8 + u;
+                    xv[u] = (pv && gi < n) ? __ldg(col + (size_t)gi * est) : 0.f;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        float r1[2], r2[2];
+                        __nv_bfloat16 a0[2], a1[2], a2[2];
+#pragma unroll
+                        for (int v = 0; v < 2; ++v) {
+                            const float x = xv[h * 8 + u + v];
+                            a0[v] = __float2bfloat16_rn(x);
+                            r1[v] = x - __bfloat162float(a0[v]);
+                            a1[v] = __float2bfloat16_rn(r1[v]);
+                            r2[v] = r1[v] - __bfloat162float(a1[v]);
+                            a2[v] = __float2bfloat16_rn(r2[v]);
+                        }
+                        const __nv_bfloat162 p0v = __halves2bfloat162(a0[0], a0[1]);
+                        const __nv_bfloat162 p1v = __halves2bfloat162(a1[0], a1[1]);
+                        const __nv_bfloat162 p2v = __halves2bfloat162(a2[0], a2[1]);
+                        w0[u / 2] = *reinterpret_cast<const uint32_t*>(&p0v);
+                        w1[u / 2] = *reinterpret_cast<const uint32_t*>(&p1v);
+                        w2[u / 2] = *reinterpret_cast<const uint32_t*>(&p2v);
+                    }
+                    const uint32_t o = sw128_off(t, (c2 + h) * 8);  // start of the 16-byte chunk
+                    *reinterpret_cast<uint4*>(abuf + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                    *reinterpret_cast<uint4*>(abuf + CT_A_SPLIT + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                    *reinterpret_cast<uint4*>(abuf + 2 * CT_A_SPLIT + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                }
+            }
+            fence_proxy_async();  // generic-proxy stores become visible to the tensor cores
+            mbar_arrive(&a_full[a]);
+        }
+        // epilogue: tensor-memory lane = pencil; 32 consecutive outputs per tcgen05.ld
+        const int wq = warp & 3;  // the lane quarter this warp may read (warps 2..5 -> 2, 3, 0, 1)
+        int got = 0;
+        if (lane == 0) got = mbar_wait(&acc_full, 0) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+            if (lane == 0) atomicOr(&g_ctc_status, 8u);
+        } else {
+            tc_fence_after();
+            const long long pg = p0 + wq * 32 + lane;
+            const bool pv = pg < P;
+            // the diagnostic derivative goes to its target, the others to the scratch array
+            float* dst = J.kind == JOB_STORE ? J.tgt[0] + off
+                                             : p.scratch + (size_t)job * p.nsim * p.fstride + off;
+            for (int c0 = 0; c0 < nop; c0 += 32) {
+                __syncwarp();
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, r);
+                if (!pv) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < n) dst[(size_t)pg + (size_t)(c0 + j) * est] = __uint_as_float(r[j]);
+            }
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // copies issued but never consumed (only after a wait gave up) land before the CTA exits
+        for (int it = s_consumed; it < s_issued; ++it)
+            if (!mbar_wait(&b_full[it % CT_B_STAGES], (it / CT_B_STAGES) & 1)) {
+                atomicOr(&g_ctc_status, 16u);
+                break;
+            }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+    // the pass completes only after the previous one (its update kernel then adds in stream order)
+    if (p.pdl == 1) pdl_wait();
+}
+
+// The field update of the pass from the scratch derivatives: every (job, simulation, cell),
+// blockIdx.y = job x simulation; the same arithmetic as the other passes' epilogues.
+__global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
+{
+    const int job = blockIdx.y / p.nsim, sim = blockIdx.y % p.nsim;
+    const PassJob& J = p.job[job];
+    if (J.kind == JOB_STORE) return;
+    const long long P = (long long)p.nx * p.ny, cells = P * p.n;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
+    const float* d = p.scratch + (size_t)job * p.nsim * p.fstride + off;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cells;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(q / P);
+        const int pxy = (int)(q - (long long)z * P);
+        const int y = pxy / p.nx, x = pxy - y * p.nx;
+        epilogue_one(p, J, (size_t)q, z, x, y, z, d[q], off, soff);
+    }
+}
+
+}  // namespace
+
+bool circ_tc_eligible(const PassParams& p)
+{
+    return p.circ && !p.comp && p.axis == 2 && p.n >= CIRC_DIRECT_N && p.n <= CIRC_MAX_N && p.ctc && p.scratch;
+}
+
+cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st)
+{
+    if (!circ_tc_eligible(p)) return cudaErrorInvalidValue;
+    EncodeTiled fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    const int nop = (p.n + 63) / 64 * 64;
+    CircMaps maps;
+    for (int k = 0; k < 6; ++k)
+        if (!make_map(fn, &maps.m[k], p.ctc + (size_t)k * nop * nop, nop, nop, nop, 64))
+            return cudaErrorInvalidValue;
+    const long long P = (long long)p.nx * p.ny;
+    const long long grid = (long long)p.njobs * p.nsim * ((P + CT_P - 1) / CT_P);
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(circ_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CT_SMEM);
+    if (e != cudaSuccess) return e;
+    // as launch_pass_kernel, with the tensor maps as a second parameter
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(CT_THREADS);
+    cfg.dynamicSmemBytes = CT_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = p.pdl ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, circ_tc_kernel, p, maps);
+    if (e != cudaSuccess) return e;
+    const long long cells = (long long)p.nx * p.ny * p.n;
+    const long long bx = std::min<long long>((cells + 255) / 256, 152 * 8);
+    circ_tc_update_kernel<<<dim3((unsigned)bx, (unsigned)(p.njobs * p.nsim)), 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t circ_tc_status(unsigned* status)
+{
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_ctc_status, sizeof v);
+    if (e != cudaSuccess) return e;
+    *status = v;
+    if (v) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_ctc_status, &zero, sizeof zero);
+    }
+    return e;
+}
+
+}  // namespace es

@@ -242,6 +242,8 @@ struct es_model {
     float2 *tw[3] = {}, *hp[3] = {}, *hm[3] = {};
     float *ckp[3] = {}, *ckm[3] = {};  // circulant kernels (axes without an FFT pass)
     float *ckp_lo[3] = {}, *ckm_lo[3] = {};  // their low parts (compensated mode)
+    __nv_bfloat16* ctc[3] = {};               // long circulant axes: kernel matrices split in three BF16 parts
+    float* ctc_scratch = nullptr;             // their z pass's derivatives [job][sim][cell] (circ_tc.cu)
     int prec = ES_PREC_FP32;
     // Kelvin-Voigt viscosity (chi = tau lambda, eta = tau mu): v^{n-1/2} kept per velocity
     // component and the stress passes' combined source w = (dt + tau) v^{n+1/2} - tau v^{n-1/2},
@@ -360,6 +362,32 @@ cudaError_t upload_axis_tables(es_model* m, int a)
         if (e == cudaSuccess) e = cudaMemcpy(m->ckm[a], hi.data() + n, n * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(m->ckp_lo[a], hi.data() + 2 * n, n * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(m->ckm_lo[a], hi.data() + 3 * n, n * 4, cudaMemcpyHostToDevice);
+        // long axes: the dense kernel matrices C[o][i] = c[(o - i) mod n] of D+ and D-, padded to
+        // whole 64-row boxes and split into three BF16 parts (c = c0 + c1 + c2 to about 2^-24) for
+        // the tensor-core pass
+        if (e == cudaSuccess && n >= CIRC_DIRECT_N && n <= CIRC_MAX_N) {
+            const int np = (n + 63) / 64 * 64;
+            const size_t mat = (size_t)np * np;
+            std::vector<__nv_bfloat16> sp(6 * mat, __float2bfloat16(0.f));
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                const std::vector<double>& ck = sgn == 0 ? ckp : ckm;
+                for (int o = 0; o < n; ++o)
+                    for (int i = 0; i < n; ++i) {
+                        const double x = ck[(size_t)(((o - i) % n + n) % n)];
+                        const __nv_bfloat16 h0 = __double2bfloat16(x);
+                        const double r1 = x - (double)__bfloat162float(h0);
+                        const __nv_bfloat16 h1 = __double2bfloat16(r1);
+                        const double r2 = r1 - (double)__bfloat162float(h1);
+                        const size_t q = (size_t)o * np + i;
+                        sp[(size_t)(3 * sgn) * mat + q] = h0;
+                        sp[(size_t)(3 * sgn + 1) * mat + q] = h1;
+                        sp[(size_t)(3 * sgn + 2) * mat + q] = __double2bfloat16(r2);
+                    }
+            }
+            if (!m->ctc[a]) e = cudaMalloc(&m->ctc[a], sp.size() * sizeof(__nv_bfloat16));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(m->ctc[a], sp.data(), sp.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+        }
     }
     return e;
 }
@@ -381,6 +409,8 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.ckm = m->ckm[axis];
     p.ckp_lo = m->ckp_lo[axis];
     p.ckm_lo = m->ckm_lo[axis];
+    p.ctc = m->ctc[axis];
+    p.scratch = axis == 2 ? m->ctc_scratch : nullptr;
     p.circ = circ_axis(m, axis) ? 1 : 0;
     p.comp = m->prec == ES_PREC_COMPENSATED ? 1 : 0;
     p.pc = m->pc[axis];
@@ -549,6 +579,17 @@ int alloc_fields(es_model* m, int nsim)
         for (int f = 0; f < NFIELD; ++f)
             m->slab[a][f] = (m->L > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4 * (size_t)nsim) : nullptr;
     CK(cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice));
+    // a long z axis without an FFT plan runs its passes on the tensor cores, whose derivatives go
+    // through this buffer to the field-update kernel
+    cudaFree(m->ctc_scratch);
+    m->ctc_scratch = nullptr;
+    if (m->nz >= CIRC_DIRECT_N && m->nz <= CIRC_MAX_N && !fft_axis(m->nz, m->nx)) {
+        e = cudaMalloc(&m->ctc_scratch, 3 * m->ncell * (size_t)nsim * sizeof(float));
+        if (e != cudaSuccess) {
+            m->ctc_scratch = nullptr;
+            return cuda_fail(e, "cudaMalloc(derivative scratch)");
+        }
+    }
     return ES_OK;
 }
 
@@ -642,6 +683,8 @@ void es_model_destroy(es_model* m)
     cudaFree(m->d_rcv);
     cudaFree(m->pool);
     cudaFree(m->fpool);
+    for (auto* c : m->ctc) cudaFree(c);
+    cudaFree(m->ctc_scratch);
     for (auto& e : m->ev)
         if (e) cudaEventDestroy(e);
     delete m;
@@ -1288,7 +1331,9 @@ int es_kernels_per_step(const es_model* m)
 {
     if (!m) return ES_ERR_ARG;
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
-    return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0);
+    // a z axis on the tensor cores adds a field-update kernel to each of its two passes
+    const bool ztc = m->prec == ES_PREC_FP32 && m->ctc_scratch && m->ctc[2];
+    return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0) + (ztc ? 2 : 0);
 }
 
 int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv)

@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernel and host translation units of
 // libes.so.  Nothing here is part of the public C ABI (include/es.h).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -54,6 +55,9 @@ struct PassParams {
     int nsim;             // independent simulations sharing the materials
     long long fstride;    // elements between consecutive simulations' field arrays
     long long sstride;    // elements between consecutive simulations' slab arrays (this axis)
+    const __nv_bfloat16* ctc;  // long circulant axes: the kernel matrices split in three BF16 parts,
+                               // [D+, D-][split][outputs][inputs], each pad64(n) x pad64(n) (circ_tc.cu)
+    float* scratch;            // that pass's derivatives, [job][sim][cell], before the field update
 };
 
 // Plan of the two-stage FFT for an axis length (0 if unsupported).
@@ -67,7 +71,15 @@ int plan_select(int kind, int n, int ra, int rb);
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
 // Longest axis the circulant pass takes (shared tiles of 2 x 32 x pad(n) floats).
 constexpr int CIRC_MAX_N = 512;
+// From this length on, the circulant passes along y and z run their epilogue from the
+// registers, and along z in FP32 mode on the tensor cores (circ_tc.cu).
+constexpr int CIRC_DIRECT_N = 192;
 cudaError_t launch_circ(const PassParams& p, cudaStream_t st);
+// The circulant pass on the tensor cores (long z axes, FP32 mode; circ_tc.cu).
+bool circ_tc_eligible(const PassParams& p);
+cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st);
+// reads and clears its device status word (bits set by waits that gave up)
+cudaError_t circ_tc_status(unsigned* status);
 cudaError_t prepare_circ_kernels();
 // Opts every pass kernel into the shared memory it needs (once per device).
 cudaError_t prepare_pass_kernels();
