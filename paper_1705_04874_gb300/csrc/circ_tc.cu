@@ -13,15 +13,17 @@
 // most 2 are accumulated in FP32 in tensor memory; the three dropped products
 // are below 2^-24 of the result, the size of FP32 rounding.
 //
-// One CTA per tile of 128 pencils and one job, 6 warps:
+// One CTA per tile of 128 pencils and one job, 10 warps:
 //   warp 0, one thread: TMA producer of the kernel-matrix splits, in chunks
 //       of up to 256 outputs x 64 inputs, through a 3-stage ring;
 //   warp 1: allocates tensor memory; one thread issues tcgen05.mma (M 128,
 //       N 256 or 64, K 16) into the accumulator (columns = outputs);
-//   warps 2-5: converters -- per k-block of 64 inputs they load the field
-//       block (coalesced along the pencils), split it, and write the three
-//       128 x 64 BF16 tiles in the 128-byte-swizzled K-major layout the MMA
-//       reads (double-buffered); then the epilogue: tensor-memory lane =
+//   warps 2-9: converters -- per k-block of 64 inputs they load the field
+//       block (coalesced along the pencils; a thread's 32 loads of a block all
+//       in flight at once), split it, and write the three 128 x 64 BF16 tiles
+//       in the 128-byte-swizzled K-major layout the MMA reads
+//       (double-buffered); then the epilogue (two warps per lane quarter,
+//       each half of the output columns): tensor-memory lane =
 //       pencil, so each tcgen05.ld gives a thread 32 consecutive outputs of
 //       its pencil, and a warp stores 32 consecutive cells of the derivative
 //       per instruction into a scratch array (plain stores: nothing to wait
@@ -50,8 +52,8 @@ constexpr int CT_A_BUF = 3 * CT_A_SPLIT;    // 48 KB per k-block
 constexpr int CT_B_STAGE = CT_OC * CT_K * 2;  // 32 KB: one split of one output chunk
 constexpr int CT_B_STAGES = 3;
 constexpr int CT_SMEM = 2 * CT_A_BUF + CT_B_STAGES * CT_B_STAGE + 1024;
-constexpr int CT_THREADS = 192;
-constexpr int CT_CONV = 128;                // converter / epilogue threads (warps 2-5)
+constexpr int CT_THREADS = 320;
+constexpr int CT_CONV = 256;                // converter / epilogue threads (warps 2-9)
 
 __device__ unsigned g_ctc_status;  // bit 0 producer, 1 MMA, 2 converter, 3 epilogue, 4 drain gave up
 
@@ -200,54 +202,52 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
             if (t == 0 && !mbar_wait(&a_empty[a], ((kb >> 1) & 1) ^ 1)) atomicOr(&g_ctc_status, 4u);
             asm volatile("bar.sync 1, %0;" ::"r"(CT_CONV) : "memory");
             uint8_t* abuf = gbase + a * CT_A_BUF;
-            // thread t owns pencil t of the tile: 16 loads in flight (coalesced over the threads),
-            // then each group of 8 consecutive inputs goes out as one 16-byte store per split (one
-            // swizzle chunk; the 8 rows of a quarter-warp hit 8 distinct bank groups)
-            const long long pg = p0 + t;
+            // thread t owns pencil t mod 128 and inputs 32 (t / 128) .. +31 of the block: its 32 loads
+            // in flight at once (coalesced over the threads), then each group of 8 consecutive inputs
+            // goes out as one 16-byte store per split (one swizzle chunk; the 8 rows of a quarter-warp
+            // hit 8 distinct bank groups)
+            const int pr = t & (CT_P - 1), half = t >> 7;
+            const long long pg = p0 + pr;
             const bool pv = pg < P;
             const float* col = J.src + off + (size_t)(pv ? pg : 0);
-#pragma unroll 1
-            for (int c2 = 0; c2 < CT_K / 8; c2 += 2) {
-                float xv[16];
+            float xv[32];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int gi = kb * CT_K + c2 * 8 + u;
-                    xv[u] = (pv && gi < n) ? __ldg(col + (size_t)gi * est) : 0.f;
-                }
+            for (int u = 0; u < 32; ++u) {
+                const int gi = kb * CT_K + half * 32 + u;
+                xv[u] = (pv && gi < n) ? __ldg(col + (size_t)gi * est) : 0.f;
+            }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t w0[4], w1[4], w2[4];
+            for (int h = 0; h < 4; ++h) {
+                uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
-                        float r1[2], r2[2];
-                        __nv_bfloat16 a0[2], a1[2], a2[2];
+                for (int u = 0; u < 8; u += 2) {
+                    __nv_bfloat16 a0[2], a1[2], a2[2];
 #pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            const float x = xv[h * 8 + u + v];
-                            a0[v] = __float2bfloat16_rn(x);
-                            r1[v] = x - __bfloat162float(a0[v]);
-                            a1[v] = __float2bfloat16_rn(r1[v]);
-                            r2[v] = r1[v] - __bfloat162float(a1[v]);
-                            a2[v] = __float2bfloat16_rn(r2[v]);
-                        }
-                        const __nv_bfloat162 p0v = __halves2bfloat162(a0[0], a0[1]);
-                        const __nv_bfloat162 p1v = __halves2bfloat162(a1[0], a1[1]);
-                        const __nv_bfloat162 p2v = __halves2bfloat162(a2[0], a2[1]);
-                        w0[u / 2] = *reinterpret_cast<const uint32_t*>(&p0v);
-                        w1[u / 2] = *reinterpret_cast<const uint32_t*>(&p1v);
-                        w2[u / 2] = *reinterpret_cast<const uint32_t*>(&p2v);
+                    for (int v = 0; v < 2; ++v) {
+                        const float x = xv[h * 8 + u + v];
+                        a0[v] = __float2bfloat16_rn(x);
+                        const float r1 = x - __bfloat162float(a0[v]);
+                        a1[v] = __float2bfloat16_rn(r1);
+                        a2[v] = __float2bfloat16_rn(r1 - __bfloat162float(a1[v]));
                     }
-                    const uint32_t o = sw128_off(t, (c2 + h) * 8);  // start of the 16-byte chunk
-                    *reinterpret_cast<uint4*>(abuf + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                    *reinterpret_cast<uint4*>(abuf + CT_A_SPLIT + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                    *reinterpret_cast<uint4*>(abuf + 2 * CT_A_SPLIT + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                    const __nv_bfloat162 p0v = __halves2bfloat162(a0[0], a0[1]);
+                    const __nv_bfloat162 p1v = __halves2bfloat162(a1[0], a1[1]);
+                    const __nv_bfloat162 p2v = __halves2bfloat162(a2[0], a2[1]);
+                    w0[u / 2] = *reinterpret_cast<const uint32_t*>(&p0v);
+                    w1[u / 2] = *reinterpret_cast<const uint32_t*>(&p1v);
+                    w2[u / 2] = *reinterpret_cast<const uint32_t*>(&p2v);
                 }
+                const uint32_t o = sw128_off(pr, half * 32 + h * 8);  // start of the 16-byte chunk
+                *reinterpret_cast<uint4*>(abuf + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4*>(abuf + CT_A_SPLIT + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                *reinterpret_cast<uint4*>(abuf + 2 * CT_A_SPLIT + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
             }
             fence_proxy_async();  // generic-proxy stores become visible to the tensor cores
             mbar_arrive(&a_full[a]);
         }
         // epilogue: tensor-memory lane = pencil; 32 consecutive outputs per tcgen05.ld
-        const int wq = warp & 3;  // the lane quarter this warp may read (warps 2..5 -> 2, 3, 0, 1)
+        const int wq = warp & 3;  // the lane quarter this warp may read (warps 2..9 -> 2, 3, 0, 1, 2, ...)
+        const int ch = (warp - 2) >> 2;  // which half of the 32-column groups: warps 2-5 and 6-9
         int got = 0;
         if (lane == 0) got = mbar_wait(&acc_full, 0) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
             // the diagnostic derivative goes to its target, the others to the scratch array
             float* dst = J.kind == JOB_STORE ? J.tgt[0] + off
                                              : p.scratch + (size_t)job * p.nsim * p.fstride + off;
-            for (int c0 = 0; c0 < nop; c0 += 32) {
+            for (int c0 = ch * 32; c0 < nop; c0 += 64) {
                 __syncwarp();
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, r);
@@ -292,23 +292,28 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
     if (p.pdl == 1) pdl_wait();
 }
 
-// The field update of the pass from the scratch derivatives: every (job, simulation, cell),
-// blockIdx.y = job x simulation; the same arithmetic as the other passes' epilogues.
+// The field update of the pass from the scratch derivatives: blockIdx.x over the
+// pencils (x + nx y), blockIdx.y over groups of 4 positions along z, blockIdx.z = job x
+// simulation; the same arithmetic as the other passes' epilogues.  Along z the slab index
+// is (x + nx y) + nx ny sp, so the pencil offset goes in as x with y = 0 (no division).
+constexpr int UPD_Z = 4;
 __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
 {
-    const int job = blockIdx.y / p.nsim, sim = blockIdx.y % p.nsim;
+    const int job = blockIdx.z / p.nsim, sim = blockIdx.z % p.nsim;
     const PassJob& J = p.job[job];
     if (J.kind == JOB_STORE) return;
-    const long long P = (long long)p.nx * p.ny, cells = P * p.n;
+    const int P = p.nx * p.ny;
+    const int pxy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pxy >= P) return;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const float* d = p.scratch + (size_t)job * p.nsim * p.fstride + off;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cells;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int z = (int)(q / P);
-        const int pxy = (int)(q - (long long)z * P);
-        const int y = pxy / p.nx, x = pxy - y * p.nx;
-        epilogue_one(p, J, (size_t)q, z, x, y, z, d[q], off, soff);
-    }
+    const int z0 = blockIdx.y * UPD_Z;
+    float dv[UPD_Z];
+#pragma unroll
+    for (int k = 0; k < UPD_Z; ++k) dv[k] = z0 + k < p.n ? d[(size_t)pxy + (size_t)(z0 + k) * P] : 0.f;
+#pragma unroll
+    for (int k = 0; k < UPD_Z; ++k)
+        if (z0 + k < p.n) epilogue_one(p, J, (size_t)pxy + (size_t)(z0 + k) * P, z0 + k, pxy, 0, z0 + k, dv[k], off, soff);
 }
 
 }  // namespace
@@ -346,9 +351,9 @@ cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st)
     cfg.numAttrs = p.pdl ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, circ_tc_kernel, p, maps);
     if (e != cudaSuccess) return e;
-    const long long cells = (long long)p.nx * p.ny * p.n;
-    const long long bx = std::min<long long>((cells + 255) / 256, 152 * 8);
-    circ_tc_update_kernel<<<dim3((unsigned)bx, (unsigned)(p.njobs * p.nsim)), 256, 0, st>>>(p);
+    circ_tc_update_kernel<<<dim3((unsigned)((P + 127) / 128), (unsigned)((p.n + UPD_Z - 1) / UPD_Z),
+                                 (unsigned)(p.njobs * p.nsim)),
+                            128, 0, st>>>(p);
     return cudaGetLastError();
 }
 
