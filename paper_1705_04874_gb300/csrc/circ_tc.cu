@@ -1,6 +1,6 @@
-// Circulant derivative passes on the fifth-generation tensor cores, for long
-// z axes without an FFT plan (n from CIRC_DIRECT_N to 512, FP32 mode; the
-// paper's 301-cell axis).  Along the axis the staggered derivative is the
+// Circulant derivative passes on the fifth-generation tensor cores, for axes
+// without an FFT plan of CIRC_TC_N to 512 cells in FP32 mode (all three axes
+// of the paper's 125 x 75 x 301 grid).  Along the axis the staggered derivative is the
 // dense contraction out[o][p] = sum_i C[o][i] f[i][p] (circulant C, pencils
 // p), so it runs as a tcgen05 GEMM whose A operand is a tile of 128 pencils
 // (the field, K = inputs) and whose B operand is the kernel matrix (N =
@@ -73,6 +73,23 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k)
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + ((k & 7) << 1));
 }
 
+// Pencils of a pass along `axis`: z: x + nx y; y: x + nx z; x: the line y + ny z.
+__host__ __device__ inline long long pass_pencils(const PassParams& p)
+{
+    return p.axis == 2 ? (long long)p.nx * p.ny : p.axis == 1 ? (long long)p.nx * p.nz : (long long)p.ny * p.nz;
+}
+// stride between consecutive positions of a pencil, and the linear index of its position 0
+__device__ __forceinline__ size_t pass_stride(const PassParams& p)
+{
+    return p.axis == 2 ? (size_t)p.nx * p.ny : p.axis == 1 ? (size_t)p.nx : (size_t)1;
+}
+__device__ __forceinline__ size_t pencil_base(const PassParams& p, long long pl)
+{
+    if (p.axis == 2) return (size_t)pl;
+    if (p.axis == 1) return (size_t)(pl % p.nx) + (size_t)p.nx * p.ny * (size_t)(pl / p.nx);
+    return (size_t)pl * p.nx;
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_constant__ PassParams p,
@@ -91,14 +108,14 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
     const int n = p.n, nkb = (n + CT_K - 1) / CT_K;
     const int nop = (n + 63) / 64 * 64;                 // outputs padded to whole 64-row boxes
     const int noc = (nop + CT_OC - 1) / CT_OC;         // output chunks
-    const long long P = (long long)p.nx * p.ny;        // pencils of the z pass (x + nx y)
+    const long long P = pass_pencils(p);
     const int ntile = (int)((P + CT_P - 1) / CT_P);
     const int u = blockIdx.x;
     const int job = u / (p.nsim * ntile), rr = u % (p.nsim * ntile);
     const int sim = rr % p.nsim, tile = rr / p.nsim;
     const long long p0 = (long long)tile * CT_P;
     const PassJob& J = p.job[job];
-    const size_t est = (size_t)p.nx * p.ny;
+    const size_t est = pass_stride(p);
     const size_t off = (size_t)sim * p.fstride;
 
     if (threadIdx.x == 0) {
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
             const int pr = t & (CT_P - 1), half = t >> 7;
             const long long pg = p0 + pr;
             const bool pv = pg < P;
-            const float* col = J.src + off + (size_t)(pv ? pg : 0);
+            const float* col = J.src + off + pencil_base(p, pv ? pg : 0);
             float xv[32];
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
@@ -257,6 +274,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
             tc_fence_after();
             const long long pg = p0 + wq * 32 + lane;
             const bool pv = pg < P;
+            const size_t pb = pencil_base(p, pv ? pg : 0);
             // the diagnostic derivative goes to its target, the others to the scratch array
             float* dst = J.kind == JOB_STORE ? J.tgt[0] + off
                                              : p.scratch + (size_t)job * p.nsim * p.fstride + off;
@@ -267,7 +285,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
                 if (!pv) continue;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    if (c0 + j < n) dst[(size_t)pg + (size_t)(c0 + j) * est] = __uint_as_float(r[j]);
+                    if (c0 + j < n) dst[pb + (size_t)(c0 + j) * est] = __uint_as_float(r[j]);
             }
         }
     }
@@ -297,6 +315,39 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
 // simulation; the same arithmetic as the other passes' epilogues.  Along z the slab index
 // is (x + nx y) + nx ny sp, so the pencil offset goes in as x with y = 0 (no division).
 constexpr int UPD_Z = 4;
+
+// x and y passes: cell-linear (coalesced), 4 cells per thread spaced by the grid
+// size; the coordinates come from the linear index.  The slab index along y is
+// x + nx (sp + S z); along x it is sp + S (y + ny z), so the line goes in as y with z = 0.
+__global__ void circ_tc_update_xy_kernel(const __grid_constant__ PassParams p)
+{
+    const int job = blockIdx.y / p.nsim, sim = blockIdx.y % p.nsim;
+    const PassJob& J = p.job[job];
+    if (J.kind == JOB_STORE) return;
+    const unsigned cells = (unsigned)p.nx * p.ny * p.nz;
+    const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
+    const float* d = p.scratch + (size_t)job * p.nsim * p.fstride + off;
+    const unsigned stride = gridDim.x * blockDim.x;
+    unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q0 < cells; q0 += UPD_Z * stride) {
+        float dv[UPD_Z];
+#pragma unroll
+        for (int k = 0; k < UPD_Z; ++k) {
+            const unsigned q = q0 + k * stride;
+            dv[k] = q < cells ? d[q] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < UPD_Z; ++k) {
+            const unsigned q = q0 + k * stride;
+            if (q >= cells) break;
+            const unsigned x = q % p.nx, line = q / p.nx;
+            if (p.axis == 0)
+                epilogue_one(p, J, q, (int)x, (int)x, (int)line, 0, dv[k], off, soff);
+            else
+                epilogue_one(p, J, q, (int)(line % p.ny), (int)x, (int)(line % p.ny), (int)(line / p.ny), dv[k], off, soff);
+        }
+    }
+}
 __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
 {
     const int job = blockIdx.z / p.nsim, sim = blockIdx.z % p.nsim;
@@ -320,7 +371,8 @@ __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
 
 bool circ_tc_eligible(const PassParams& p)
 {
-    return p.circ && !p.comp && p.axis == 2 && p.n >= CIRC_DIRECT_N && p.n <= CIRC_MAX_N && p.ctc && p.scratch;
+    return p.circ && !p.comp && p.n >= CIRC_TC_N && p.n <= CIRC_MAX_N && p.ctc && p.scratch &&
+           (long long)p.nx * p.ny * p.nz < (1LL << 31);
 }
 
 cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st)
@@ -333,7 +385,7 @@ cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st)
     for (int k = 0; k < 6; ++k)
         if (!make_map(fn, &maps.m[k], p.ctc + (size_t)k * nop * nop, nop, nop, nop, 64))
             return cudaErrorInvalidValue;
-    const long long P = (long long)p.nx * p.ny;
+    const long long P = pass_pencils(p);
     const long long grid = (long long)p.njobs * p.nsim * ((P + CT_P - 1) / CT_P);
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(circ_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CT_SMEM);
@@ -351,9 +403,15 @@ cudaError_t launch_circ_tc(const PassParams& p, cudaStream_t st)
     cfg.numAttrs = p.pdl ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, circ_tc_kernel, p, maps);
     if (e != cudaSuccess) return e;
-    circ_tc_update_kernel<<<dim3((unsigned)((P + 127) / 128), (unsigned)((p.n + UPD_Z - 1) / UPD_Z),
-                                 (unsigned)(p.njobs * p.nsim)),
-                            128, 0, st>>>(p);
+    if (p.axis == 2) {
+        circ_tc_update_kernel<<<dim3((unsigned)((P + 127) / 128), (unsigned)((p.n + UPD_Z - 1) / UPD_Z),
+                                     (unsigned)(p.njobs * p.nsim)),
+                                128, 0, st>>>(p);
+    } else {
+        const long long cells = (long long)p.nx * p.ny * p.nz;
+        const long long bx = std::max<long long>(1, std::min<long long>((cells + 256 * UPD_Z - 1) / (256 * UPD_Z), 152 * 16));
+        circ_tc_update_xy_kernel<<<dim3((unsigned)bx, (unsigned)(p.njobs * p.nsim)), 256, 0, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -365,7 +365,7 @@ cudaError_t upload_axis_tables(es_model* m, int a)
         // long axes: the dense kernel matrices C[o][i] = c[(o - i) mod n] of D+ and D-, padded to
         // whole 64-row boxes and split into three BF16 parts (c = c0 + c1 + c2 to about 2^-24) for
         // the tensor-core pass
-        if (e == cudaSuccess && n >= CIRC_DIRECT_N && n <= CIRC_MAX_N) {
+        if (e == cudaSuccess && n >= CIRC_TC_N && n <= CIRC_MAX_N) {
             const int np = (n + 63) / 64 * 64;
             const size_t mat = (size_t)np * np;
             std::vector<__nv_bfloat16> sp(6 * mat, __float2bfloat16(0.f));
@@ -410,7 +410,7 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.ckp_lo = m->ckp_lo[axis];
     p.ckm_lo = m->ckm_lo[axis];
     p.ctc = m->ctc[axis];
-    p.scratch = axis == 2 ? m->ctc_scratch : nullptr;
+    p.scratch = m->ctc_scratch;
     p.circ = circ_axis(m, axis) ? 1 : 0;
     p.comp = m->prec == ES_PREC_COMPENSATED ? 1 : 0;
     p.pc = m->pc[axis];
@@ -579,11 +579,16 @@ int alloc_fields(es_model* m, int nsim)
         for (int f = 0; f < NFIELD; ++f)
             m->slab[a][f] = (m->L > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4 * (size_t)nsim) : nullptr;
     CK(cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice));
-    // a long z axis without an FFT plan runs its passes on the tensor cores, whose derivatives go
-    // through this buffer to the field-update kernel
+    // axes of CIRC_TC_N cells or more without an FFT plan run their passes on the tensor cores,
+    // whose derivatives go through this buffer to the field-update kernel
     cudaFree(m->ctc_scratch);
     m->ctc_scratch = nullptr;
-    if (m->nz >= CIRC_DIRECT_N && m->nz <= CIRC_MAX_N && !fft_axis(m->nz, m->nx)) {
+    bool tc = false;
+    for (int a = 0; a < 3; ++a) {
+        const int n = axis_len(m, a);
+        tc |= n >= CIRC_TC_N && n <= CIRC_MAX_N && !fft_axis(n, m->nx);
+    }
+    if (tc) {
         e = cudaMalloc(&m->ctc_scratch, 3 * m->ncell * (size_t)nsim * sizeof(float));
         if (e != cudaSuccess) {
             m->ctc_scratch = nullptr;
@@ -1331,9 +1336,13 @@ int es_kernels_per_step(const es_model* m)
 {
     if (!m) return ES_ERR_ARG;
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
-    // a z axis on the tensor cores adds a field-update kernel to each of its two passes
-    const bool ztc = m->prec == ES_PREC_FP32 && m->ctc_scratch && m->ctc[2];
-    return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0) + (ztc ? 2 : 0);
+    // an axis on the tensor cores adds a field-update kernel to each of its two passes
+    int tc = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int n = axis_len(m, a);
+        tc += m->prec == ES_PREC_FP32 && m->ctc_scratch && m->ctc[a] && !fft_axis(n, m->nx) ? 2 : 0;
+    }
+    return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0) + tc;
 }
 
 int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv)

@@ -71,9 +71,13 @@ int plan_select(int kind, int n, int ra, int rb);
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
 // Longest axis the circulant pass takes (shared tiles of 2 x 32 x pad(n) floats).
 constexpr int CIRC_MAX_N = 512;
-// From this length on, the circulant passes along y and z run their epilogue from the
-// registers, and along z in FP32 mode on the tensor cores (circ_tc.cu).
+// From this length on, the CUDA-core circulant passes along y and z run their epilogue from
+// the registers.
 constexpr int CIRC_DIRECT_N = 192;
+// From this length on, circulant passes in FP32 mode run on the tensor cores (circ_tc.cu):
+// below it the CUDA-core pass is faster (measured at 75 and 125 cells: the scratch round trip
+// and the separate update kernel cost more than the O(n) multiply-adds they replace).
+constexpr int CIRC_TC_N = 192;
 cudaError_t launch_circ(const PassParams& p, cudaStream_t st);
 // The circulant pass on the tensor cores (long z axes, FP32 mode; circ_tc.cu).
 bool circ_tc_eligible(const PassParams& p);

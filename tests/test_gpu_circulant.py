@@ -152,15 +152,15 @@ def test_compensated_run_with_a_long_circulant_axis(es, orc):
 
 
 @pytest.mark.parametrize("shape,pml,nb", [((200, 16, 32), 3, 1), ((193, 12, 20), 3, 1), ((301, 12, 24), 4, 2),
-                                          ((512, 4, 8), 0, 1)])
-def test_tensor_core_z_passes_match_oracle(es, orc, shape, pml, nb):
-    """z axes of 192 to 512 cells without an FFT plan run their passes on the
+                                          ((512, 4, 8), 0, 1), ((16, 200, 24), 3, 1), ((12, 12, 201), 3, 1)])
+def test_tensor_core_passes_match_oracle(es, orc, shape, pml, nb):
+    """Axes of 192 to 512 cells without an FFT plan run their passes on the
     tensor cores in FP32 mode (field and kernel split in three BF16 parts,
     six products, FP32 accumulation; the update in a separate kernel): the
     first simulation against the oracle (median trace error below 1e-4, every
     field within 1e-4), the others of a batch equal to single-source runs bit
-    for bit.  Covers the shortest such axis (193), the longest (512, no PML)
-    and the PML along z."""
+    for bit.  Long z axes (the shortest such, 193, and the longest, 512, no
+    PML), a long y axis and a long odd x axis, with the PML along each."""
     rho, cp, cs = synth.marine_model(shape=shape, seed=sum(shape))
     nt = 60
     dt = cfl_dt(cp, 10.0)
