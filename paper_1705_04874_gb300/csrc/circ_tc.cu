@@ -1,10 +1,10 @@
 // Circulant derivative passes on the fifth-generation tensor cores, for axes
-// without an FFT plan of CIRC_TC_N to 512 cells in FP32 mode (all three axes
-// of the paper's 125 x 75 x 301 grid).  Along the axis the staggered derivative is the
-// dense contraction out[o][p] = sum_i C[o][i] f[i][p] (circulant C, pencils
-// p), so it runs as a tcgen05 GEMM whose A operand is a tile of 128 pencils
-// (the field, K = inputs) and whose B operand is the kernel matrix (N =
-// outputs, K = inputs).
+// without an FFT plan of CIRC_TC_N (192) to 512 cells in FP32 mode (the
+// 301-cell axis of the paper's 125 x 75 x 301 grid).  Along the axis the
+// staggered derivative is the dense contraction out[o][p] = sum_i C[o][i]
+// f[i][p] (circulant C, pencils p), so it runs as a tcgen05 GEMM whose A
+// operand is a tile of 128 pencils (the field, K = inputs) and whose B operand
+// is the kernel matrix (N = outputs, K = inputs).
 //
 // FP32 accuracy from BF16 products: each field value is split exactly into
 // three BF16 parts (f = f0 + f1 + f2, computed in FP32 by the converter
@@ -17,7 +17,8 @@
 //   warp 0, one thread: TMA producer of the kernel-matrix splits, in chunks
 //       of up to 256 outputs x 64 inputs, through a 3-stage ring;
 //   warp 1: allocates tensor memory; one thread issues tcgen05.mma (M 128,
-//       N 256 or 64, K 16) into the accumulator (columns = outputs);
+//       N 256 or the remaining outputs, a multiple of 64; K 16) into the
+//       accumulator (columns = outputs);
 //   warps 2-9: converters -- per k-block of 64 inputs they load the field
 //       block (coalesced along the pencils; a thread's 32 loads of a block all
 //       in flight at once), split it, and write the three 128 x 64 BF16 tiles
@@ -28,9 +29,10 @@
 //       its pencil, and a warp stores 32 consecutive cells of the derivative
 //       per instruction into a scratch array (plain stores: nothing to wait
 //       for).  The field update with its PML splits then runs as a separate
-//       element-wise kernel at full occupancy (circ_tc_update_kernel): done
-//       here by the four epilogue warps of one CTA per SM, its dependent
-//       coefficient loads made the pass latency-bound.
+//       element-wise kernel at full occupancy (circ_tc_update_kernel along z,
+//       circ_tc_update_xy_kernel along x and y): done here by the few
+//       epilogue warps of one CTA per SM, its dependent coefficient loads made
+//       the pass latency-bound.
 // Every mbarrier wait is bounded; a wait that runs out records a status bit
 // (circ_tc_status) and the CTA finishes.
 #include <algorithm>
