@@ -62,16 +62,25 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
                     double dx, int pml, es_model** out);
 
 /* Arithmetic of the spatial derivatives (the fields are FP32 either way).
- * ES_PREC_FP32 (default): fused FFT passes where an axis has a plan, FP32
- * circulant passes elsewhere.  ES_PREC_COMPENSATED: every axis through the
- * circulant passes with error-free transformations (each product split exactly
- * by one FMA, Knuth's TwoSum on the running sum, the kernel row as FP32 high
- * plus low parts), so each derivative is accurate to about twice FP32's
- * precision and only the FP32 storage of the fields limits the traces (O(n)
- * work per element, about 10 FP32 operations per multiply-add).  Applies from
- * the next es_run.  ES_ERR_ARG for any other mode. */
+ * ES_PREC_FP32 (default): fused FFT passes where an axis has a plan (each
+ * derivative as a 10-point near stencil in FP32 plus the FFT of the rest of
+ * the operator, which confines FP32 FFT roundoff to about 1 % of its plain
+ * size), FP32 circulant passes on the CUDA cores elsewhere.
+ * ES_PREC_COMPENSATED: every axis through the circulant passes with
+ * error-free transformations (each product split exactly by one FMA, Knuth's
+ * TwoSum on the running sum, the kernel row as FP32 high plus low parts), so
+ * each derivative is accurate to about twice FP32's precision and only the
+ * FP32 storage of the fields limits the traces (O(n) work per element, about
+ * 10 FP32 operations per multiply-add).  ES_PREC_FP32_TC: as ES_PREC_FP32, but
+ * circulant axes of 192 to 512 cells run as GEMMs on the tensor cores (the
+ * field and the kernel matrix split in three BF16 parts each, six products
+ * accumulated in FP32; the near stencil stays on the CUDA cores).  The paper
+ * has no tensor-core step: this mode is an opt-in speed-up for long odd axes
+ * such as the paper's 301.  Applies from the next es_run.  ES_ERR_ARG for any
+ * other mode. */
 #define ES_PREC_FP32 0
 #define ES_PREC_COMPENSATED 1
+#define ES_PREC_FP32_TC 2
 int es_model_set_precision(es_model* m, int mode);
 
 /* Kelvin-Voigt viscosity (Eq. (1)-(2): the chi and eta terms, zero in the

@@ -19,7 +19,7 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
     const bool slab = in_slab(pos, p.n, p.L);
     const int S = 2 * p.L + 1;
     if (J.kind == JOB_SINGLE) {
-        float inc = dt * __ldg(J.coef[0] + q) * d;
+        float inc = increment(dt, __ldg(J.coef[0] + q), d);
         if (slab) {
             const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
             const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
@@ -32,7 +32,7 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
         const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            float inc = dt * (lam + (t == J.diag ? 2.f * mu : 0.f)) * d;
+            float inc = increment(dt, normal_coef(lam, mu, t == J.diag), d);
             if (slab) inc = split_delta(J.slab[t], soff + si, P, inc);
             atomicAdd(J.tgt[t] + off + q, inc);
         }

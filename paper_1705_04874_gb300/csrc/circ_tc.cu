@@ -277,9 +277,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
             const long long pg = p0 + wq * 32 + lane;
             const bool pv = pg < P;
             const size_t pb = pencil_base(p, pv ? pg : 0);
-            // the diagnostic derivative goes to its target, the others to the scratch array
-            float* dst = J.kind == JOB_STORE ? J.tgt[0] + off
-                                             : p.scratch + (size_t)job * p.nsim * p.fstride + off;
+            // the far part of the derivative to the scratch array (the update kernel adds the near part)
+            float* dst = p.scratch + (size_t)job * p.nsim * p.fstride + off;
             for (int c0 = ch * 32; c0 < nop; c0 += 64) {
                 __syncwarp();
                 uint32_t r[32];
@@ -312,11 +311,18 @@ __global__ void __launch_bounds__(CT_THREADS, 1) circ_tc_kernel(const __grid_con
     if (p.pdl == 1) pdl_wait();
 }
 
-// The field update of the pass from the scratch derivatives: blockIdx.x over the
-// pencils (x + nx y), blockIdx.y over groups of 4 positions along z, blockIdx.z = job x
-// simulation; the same arithmetic as the other passes' epilogues.  Along z the slab index
-// is (x + nx y) + nx ny sp, so the pencil offset goes in as x with y = 0 (no division).
+// The field update of the pass from the scratch derivatives (the far part: the GEMM's kernel
+// matrices leave out the NEAR_TAPS central entries), plus the near stencil in FP32 from the
+// source field, then the same arithmetic as the other passes' epilogues.  Along z the slab
+// index is (x + nx y) + nx ny sp, so the pencil offset goes in as x with y = 0 (no division).
 constexpr int UPD_Z = 4;
+
+__device__ __forceinline__ void update_cell(const PassParams& p, const PassJob& J, size_t q, int pos, int x, int y,
+                                            int z, float d, size_t off, size_t soff)
+{
+    if (J.kind == JOB_STORE) J.tgt[0][off + q] = d;
+    else epilogue_one(p, J, q, pos, x, y, z, d, off, soff);
+}
 
 // x and y passes: cell-linear (coalesced), 4 cells per thread spaced by the grid
 // size; the coordinates come from the linear index.  The slab index along y is
@@ -325,10 +331,11 @@ __global__ void circ_tc_update_xy_kernel(const __grid_constant__ PassParams p)
 {
     const int job = blockIdx.y / p.nsim, sim = blockIdx.y % p.nsim;
     const PassJob& J = p.job[job];
-    if (J.kind == JOB_STORE) return;
     const unsigned cells = (unsigned)p.nx * p.ny * p.nz;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const float* d = p.scratch + (size_t)job * p.nsim * p.fstride + off;
+    const float* f = J.src + off;
+    const int ofs = near_ofs(J.sign);
     const unsigned stride = gridDim.x * blockDim.x;
     unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (; q0 < cells; q0 += UPD_Z * stride) {
@@ -343,30 +350,59 @@ __global__ void circ_tc_update_xy_kernel(const __grid_constant__ PassParams p)
             const unsigned q = q0 + k * stride;
             if (q >= cells) break;
             const unsigned x = q % p.nx, line = q / p.nx;
+            // near stencil along the pass axis (wrapped), taps in order
+            const int pos = p.axis == 0 ? (int)x : (int)(line % p.ny);
+            const size_t base = p.axis == 0 ? (size_t)line * p.nx : (size_t)q - (size_t)pos * p.nx;
+            const size_t est = p.axis == 0 ? 1 : (size_t)p.nx;
+            float s = dv[k];
+#pragma unroll
+            for (int t = 0; t < NEAR_TAPS; ++t) {
+                int i = pos + ofs + t;
+                i += i < 0 ? p.n : 0;
+                i -= i >= p.n ? p.n : 0;
+                s = fmaf(J.g[t], __ldg(f + base + (size_t)i * est), s);
+            }
             if (p.axis == 0)
-                epilogue_one(p, J, q, (int)x, (int)x, (int)line, 0, dv[k], off, soff);
+                update_cell(p, J, q, (int)x, (int)x, (int)line, 0, s, off, soff);
             else
-                epilogue_one(p, J, q, (int)(line % p.ny), (int)x, (int)(line % p.ny), (int)(line / p.ny), dv[k], off, soff);
+                update_cell(p, J, q, (int)(line % p.ny), (int)x, (int)(line % p.ny), (int)(line / p.ny), s, off, soff);
         }
     }
 }
+
+// z passes: blockIdx.x over the pencils (x + nx y), blockIdx.y over groups of UPD_Z
+// positions along z, blockIdx.z = job x simulation; the near stencil slides over the
+// UPD_Z + NEAR_TAPS - 1 inputs of the group (each read once)
 __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
 {
     const int job = blockIdx.z / p.nsim, sim = blockIdx.z % p.nsim;
     const PassJob& J = p.job[job];
-    if (J.kind == JOB_STORE) return;
     const int P = p.nx * p.ny;
     const int pxy = blockIdx.x * blockDim.x + threadIdx.x;
     if (pxy >= P) return;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const float* d = p.scratch + (size_t)job * p.nsim * p.fstride + off;
+    const float* f = J.src + off + pxy;
     const int z0 = blockIdx.y * UPD_Z;
+    const int ofs = near_ofs(J.sign);
     float dv[UPD_Z];
 #pragma unroll
     for (int k = 0; k < UPD_Z; ++k) dv[k] = z0 + k < p.n ? d[(size_t)pxy + (size_t)(z0 + k) * P] : 0.f;
 #pragma unroll
+    for (int m = 0; m < UPD_Z + NEAR_TAPS - 1; ++m) {
+        int i = z0 + ofs + m;
+        i += i < 0 ? p.n : 0;
+        i -= i >= p.n ? p.n : 0;
+        const float v = __ldg(f + (size_t)i * P);
+#pragma unroll
+        for (int k = 0; k < UPD_Z; ++k) {
+            const int t = m - k;
+            if (t >= 0 && t < NEAR_TAPS) dv[k] = fmaf(J.g[t], v, dv[k]);
+        }
+    }
+#pragma unroll
     for (int k = 0; k < UPD_Z; ++k)
-        if (z0 + k < p.n) epilogue_one(p, J, (size_t)pxy + (size_t)(z0 + k) * P, z0 + k, pxy, 0, z0 + k, dv[k], off, soff);
+        if (z0 + k < p.n) update_cell(p, J, (size_t)pxy + (size_t)(z0 + k) * P, z0 + k, pxy, 0, z0 + k, dv[k], off, soff);
 }
 
 }  // namespace

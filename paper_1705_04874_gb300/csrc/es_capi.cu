@@ -167,11 +167,16 @@ bool fft_plan(int n) { int a, b; return plan_radices(n, &a, &b) != 0; }
 bool axis_ok(int n) { return n >= 3 && n <= CIRC_MAX_N; }
 bool fft_axis(int n, int nx) { return fft_plan(n) && nx % 2 == 0; }
 
-// i kappa exp(sign i kappa d / 2) / n and exp(-2 pi i m / n), in FP64 then
-// rounded; and the circulant kernels of the two staggered derivatives,
-// c_l = sum_m H_m exp(2 pi i m l / n) (real: H is Hermitian, Nyquist included)
+// exp(-2 pi i m / n) and the staggered multipliers H = i kappa exp(sign i kappa d / 2) of
+// an axis, in FP64 then rounded.  The FFT passes evaluate D = N + far (es_internal.h):
+// g (gp for D(+), gm for D(-)) are the NEAR_TAPS kernel entries c_l at offsets
+// near_ofs(sign) .. +NEAR_TAPS-1 rounded to FP32, and the tables hold
+// (H - sum_t g_t exp(2 pi i m (near_ofs + t) / n)) / n, the FP32 taps subtracted so that
+// near + far equals D exactly up to the rounding of the tables.  Axes of NEAR_TAPS cells
+// or fewer keep the whole multiplier (g = 0).  For a circulant axis also the kernels
+// c_l = sum_m H_m / n exp(2 pi i m l / n) (real: H is Hermitian, Nyquist included).
 void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& hp, std::vector<float2>& hm,
-                 std::vector<double>* ckp = nullptr, std::vector<double>* ckm = nullptr)
+                 float* gp, float* gm, std::vector<double>* ckp = nullptr, std::vector<double>* ckm = nullptr)
 {
     const double pi = 3.14159265358979323846;
     tw.resize(n);
@@ -191,22 +196,44 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
             const double ph = (s == 0 ? 0.5 : -0.5) * kap * d;
             hr[s][m] = -kap * std::sin(ph) / n;
             hi[s][m] = kap * std::cos(ph) / n;
-            (s == 0 ? hp : hm)[m] = make_float2((float)hr[s][m], (float)hi[s][m]);
         }
+    }
+    // c_l of D(+) (s = 0) or D(-) (s = 1), angles reduced exactly in integers
+    auto kernel_entry = [&](int s, int l) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) {
+            const long long ml = ((long long)m * l) % n;
+            const double a = 2.0 * pi * (double)ml / (double)n;
+            acc += hr[s][m] * std::cos(a) - hi[s][m] * std::sin(a);
+        }
+        return acc;
+    };
+    for (int s = 0; s < 2; ++s) {
+        float* g = s == 0 ? gp : gm;
+        const int ofs = near_ofs(s == 0 ? +1 : -1);
+        std::vector<double> nr(n, 0.0), ni(n, 0.0);  // H_near / n
+        for (int t = 0; t < NEAR_TAPS; ++t) {
+            g[t] = 0.f;
+            if (n <= NEAR_TAPS) continue;
+            const int delta = ofs + t;                      // (N f)_i gains g_t f_{i + delta}
+            g[t] = (float)kernel_entry(s, ((-delta) % n + n) % n);  // (D f)_i = sum_l c_l f_{i - l}
+            for (int m = 0; m < n; ++m) {
+                const long long md = (((long long)m * delta) % n + n) % n;
+                const double a = 2.0 * pi * (double)md / (double)n;
+                nr[m] += (double)g[t] * std::cos(a) / n;
+                ni[m] += (double)g[t] * std::sin(a) / n;
+            }
+        }
+        for (int m = 0; m < n; ++m)
+            (s == 0 ? hp : hm)[m] = make_float2((float)(hr[s][m] - nr[m]), (float)(hi[s][m] - ni[m]));
     }
     if (!ckp || !ckm) return;
     ckp->resize(n);
     ckm->resize(n);
-    for (int l = 0; l < n; ++l)
-        for (int s = 0; s < 2; ++s) {
-            double acc = 0.0;
-            for (int m = 0; m < n; ++m) {
-                const long long ml = ((long long)m * l) % n;
-                const double a = 2.0 * pi * (double)ml / (double)n;
-                acc += hr[s][m] * std::cos(a) - hi[s][m] * std::sin(a);
-            }
-            (s == 0 ? *ckp : *ckm)[l] = acc;
-        }
+    for (int l = 0; l < n; ++l) {
+        (*ckp)[l] = kernel_entry(0, l);
+        (*ckm)[l] = kernel_entry(1, l);
+    }
 }
 
 struct Src {
@@ -240,6 +267,7 @@ struct es_model {
     float* mat[NMAT] = {};
     float** d_fields = nullptr;
     float2 *tw[3] = {}, *hp[3] = {}, *hm[3] = {};
+    float gp[3][NEAR_TAPS] = {}, gm[3][NEAR_TAPS] = {};  // near taps of D(+), D(-) per axis (FFT passes)
     float *ckp[3] = {}, *ckm[3] = {};  // circulant kernels (axes without an FFT pass)
     float *ckp_lo[3] = {}, *ckm_lo[3] = {};  // their low parts (compensated mode)
     __nv_bfloat16* ctc[3] = {};               // long circulant axes: kernel matrices split in three BF16 parts
@@ -345,7 +373,7 @@ cudaError_t upload_axis_tables(es_model* m, int a)
     std::vector<float2> tw, hp, hm;
     std::vector<double> ckp, ckm;
     const bool circ = circ_axis(m, a);
-    axis_tables(n, m->d[a], tw, hp, hm, circ ? &ckp : nullptr, circ ? &ckm : nullptr);
+    axis_tables(n, m->d[a], tw, hp, hm, m->gp[a], m->gm[a], circ ? &ckp : nullptr, circ ? &ckm : nullptr);
     cudaError_t e = cudaMemcpy(m->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->hp[a], hp.data(), hp.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->hm[a], hm.data(), hm.size() * 8, cudaMemcpyHostToDevice);
@@ -362,15 +390,21 @@ cudaError_t upload_axis_tables(es_model* m, int a)
         if (e == cudaSuccess) e = cudaMemcpy(m->ckm[a], hi.data() + n, n * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(m->ckp_lo[a], hi.data() + 2 * n, n * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(m->ckm_lo[a], hi.data() + 3 * n, n * 4, cudaMemcpyHostToDevice);
-        // long axes: the dense kernel matrices C[o][i] = c[(o - i) mod n] of D+ and D-, padded to
-        // whole 64-row boxes and split into three BF16 parts (c = c0 + c1 + c2 to about 2^-24) for
-        // the tensor-core pass
-        if (e == cudaSuccess && n >= CIRC_TC_N && n <= CIRC_MAX_N) {
+        // long axes on the tensor cores (ES_PREC_FP32_TC): the dense matrices C[o][i] =
+        // c[(o - i) mod n] of the far parts of D+ and D- (the kernel less its FP32 near taps, which
+        // the update kernel adds in FP32), padded to whole 64-row boxes and split into three BF16
+        // parts (c = c0 + c1 + c2 to about 2^-24)
+        if (e == cudaSuccess && m->prec == ES_PREC_FP32_TC && n >= CIRC_TC_N && n <= CIRC_MAX_N) {
             const int np = (n + 63) / 64 * 64;
             const size_t mat = (size_t)np * np;
             std::vector<__nv_bfloat16> sp(6 * mat, __float2bfloat16(0.f));
             for (int sgn = 0; sgn < 2; ++sgn) {
-                const std::vector<double>& ck = sgn == 0 ? ckp : ckm;
+                std::vector<double> ck = sgn == 0 ? ckp : ckm;
+                const float* g = sgn == 0 ? m->gp[a] : m->gm[a];
+                for (int t = 0; t < NEAR_TAPS; ++t) {
+                    const int delta = near_ofs(sgn == 0 ? +1 : -1) + t;  // (N f)_o gains g_t f_{o + delta}
+                    ck[(size_t)(((-delta) % n) + n) % n] -= (double)g[t];
+                }
                 for (int o = 0; o < n; ++o)
                     for (int i = 0; i < n; ++i) {
                         const double x = ck[(size_t)(((o - i) % n + n) % n)];
@@ -409,8 +443,8 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.ckm = m->ckm[axis];
     p.ckp_lo = m->ckp_lo[axis];
     p.ckm_lo = m->ckm_lo[axis];
-    p.ctc = m->ctc[axis];
-    p.scratch = m->ctc_scratch;
+    p.ctc = m->prec == ES_PREC_FP32_TC ? m->ctc[axis] : nullptr;
+    p.scratch = m->prec == ES_PREC_FP32_TC ? m->ctc_scratch : nullptr;
     p.circ = circ_axis(m, axis) ? 1 : 0;
     p.comp = m->prec == ES_PREC_COMPENSATED ? 1 : 0;
     p.pc = m->pc[axis];
@@ -420,10 +454,14 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.nsim = m->nsim;
     p.fstride = (long long)m->ncell;
     p.sstride = (long long)slab_count(m, axis);
+    auto taps = [&](PassJob& J) {
+        for (int t = 0; t < NEAR_TAPS; ++t) J.g[t] = J.sign > 0 ? m->gp[axis][t] : m->gm[axis][t];
+    };
     auto single = [&](PassJob& J, int src, int sign, int tgt, int coef) {
         J.src = m->f[src];
         J.kind = JOB_SINGLE;
         J.sign = sign;
+        taps(J);
         J.tgt[0] = m->f[tgt];
         J.slab[0] = m->slab[axis][tgt];
         J.coef[0] = m->mat[coef];
@@ -443,6 +481,7 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
         J.src = m->f[VX + axis];
         J.kind = JOB_NORMAL;
         J.sign = -1;
+        taps(J);
         J.diag = axis;
         for (int t = 0; t < 3; ++t) {
             J.tgt[t] = m->f[SXX + t];
@@ -555,6 +594,28 @@ int capture(es_model* m, int steps, float dt, int n_rcv, long long start, bool t
     return ES_OK;
 }
 
+// whether a pass along axis a runs on the tensor cores (ES_PREC_FP32_TC, a circulant axis of
+// CIRC_TC_N to CIRC_MAX_N cells)
+bool tc_axis(const es_model* m, int a)
+{
+    const int n = axis_len(m, a);
+    return m->prec == ES_PREC_FP32_TC && n >= CIRC_TC_N && n <= CIRC_MAX_N && !fft_axis(n, m->nx);
+}
+
+// In ES_PREC_FP32_TC mode with a tensor-core axis: the buffer through which those passes'
+// derivatives go to the field-update kernel, [job][sim][cell] (3 jobs)
+int alloc_tc_scratch(es_model* m)
+{
+    const bool tc = tc_axis(m, 0) || tc_axis(m, 1) || tc_axis(m, 2);
+    if (!tc || m->ctc_scratch) return ES_OK;
+    cudaError_t e = cudaMalloc(&m->ctc_scratch, 3 * m->ncell * (size_t)m->nsim * sizeof(float));
+    if (e != cudaSuccess) {
+        m->ctc_scratch = nullptr;
+        return cuda_fail(e, "cudaMalloc(derivative scratch)");
+    }
+    return ES_OK;
+}
+
 // (Re)allocates the field totals and slab splits for nsim simulations:
 // field f of simulation k at f[f] + k ncell, its split along axis a at
 // slab[a][f] + k slab_count(a).
@@ -579,23 +640,9 @@ int alloc_fields(es_model* m, int nsim)
         for (int f = 0; f < NFIELD; ++f)
             m->slab[a][f] = (m->L > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4 * (size_t)nsim) : nullptr;
     CK(cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice));
-    // axes of CIRC_TC_N cells or more without an FFT plan run their passes on the tensor cores,
-    // whose derivatives go through this buffer to the field-update kernel
     cudaFree(m->ctc_scratch);
     m->ctc_scratch = nullptr;
-    bool tc = false;
-    for (int a = 0; a < 3; ++a) {
-        const int n = axis_len(m, a);
-        tc |= n >= CIRC_TC_N && n <= CIRC_MAX_N && !fft_axis(n, m->nx);
-    }
-    if (tc) {
-        e = cudaMalloc(&m->ctc_scratch, 3 * m->ncell * (size_t)nsim * sizeof(float));
-        if (e != cudaSuccess) {
-            m->ctc_scratch = nullptr;
-            return cuda_fail(e, "cudaMalloc(derivative scratch)");
-        }
-    }
-    return ES_OK;
+    return alloc_tc_scratch(m);
 }
 
 int run_checked_args(es_model* m, int nt, double dt, int n_rcv)
@@ -616,7 +663,8 @@ cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, do
     const bool circ = !fft_axis(n, nx);
     std::vector<float2> tw, hp, hm;
     std::vector<double> ckp64, ckm64;
-    axis_tables(n, d, tw, hp, hm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
+    float gp[NEAR_TAPS], gm[NEAR_TAPS];
+    axis_tables(n, d, tw, hp, hm, gp, gm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
     std::vector<float> ckp(ckp64.begin(), ckp64.end()), ckm(ckm64.begin(), ckm64.end());
     float2* tab = nullptr;
     cudaError_t e = cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4);
@@ -649,6 +697,7 @@ cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, do
         p.job[0].kind = acc ? JOB_SINGLE : JOB_STORE;
         p.job[0].coef[0] = acc;
         p.job[0].sign = shift;
+        for (int t = 0; t < NEAR_TAPS; ++t) p.job[0].g[t] = shift > 0 ? gp[t] : gm[t];
         e = launch_pass(p, st);
     }
     cudaError_t e2 = cudaStreamSynchronize(st);
@@ -821,10 +870,10 @@ int es_model_set_viscosity(es_model* m, double tau)
 
 int es_model_set_precision(es_model* m, int mode)
 {
-    if (!m || (mode != ES_PREC_FP32 && mode != ES_PREC_COMPENSATED)) return ES_ERR_ARG;
+    if (!m || (mode != ES_PREC_FP32 && mode != ES_PREC_COMPENSATED && mode != ES_PREC_FP32_TC)) return ES_ERR_ARG;
     m->prec = mode;
     for (int a = 0; a < 3; ++a) CK(upload_axis_tables(m, a));
-    return ES_OK;
+    return alloc_tc_scratch(m);
 }
 
 int es_model_set_spacing(es_model* m, double dx, double dy, double dz)
@@ -1124,6 +1173,15 @@ static int run_finish(es_model* m, int nt, int n_rcv, float* traces, cudaStream_
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, m->d_int + 2, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    // a bounded wait of a tensor-core pass that ran out left its derivatives unwritten
+    if (tc_axis(m, 0) || tc_axis(m, 1) || tc_axis(m, 2)) {
+        unsigned status = 0;
+        CK(circ_tc_status(&status));
+        if (status) {
+            snprintf(g_err, sizeof g_err, "tensor-core circulant pass: a bounded wait gave up (status %#x)", status);
+            return ES_ERR_TIMEOUT;
+        }
+    }
     return flag ? ES_ERR_UNSTABLE : ES_OK;
 }
 
@@ -1338,10 +1396,7 @@ int es_kernels_per_step(const es_model* m)
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
     // an axis on the tensor cores adds a field-update kernel to each of its two passes
     int tc = 0;
-    for (int a = 0; a < 3; ++a) {
-        const int n = axis_len(m, a);
-        tc += m->prec == ES_PREC_FP32 && m->ctc_scratch && m->ctc[a] && !fft_axis(n, m->nx) ? 2 : 0;
-    }
+    for (int a = 0; a < 3; ++a) tc += tc_axis(m, a) ? 2 : 0;
     return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0) + tc;
 }
 

@@ -20,6 +20,17 @@ enum JobKind {
     JOB_NORMAL = 2   // sxx, syy, szz += dt (lambda + 2 mu [t == diag]) D
 };
 
+// The FFT passes evaluate each staggered derivative split in two:
+//   D f = N f + IFFT(H_far FFT f),  (N f)_i = sum_t g_t f_{i + t + NEAR_OFS(sign)}
+// with g the NEAR_TAPS central entries of the operator's circulant kernel and
+// H_far = H - FFT(those entries), which in exact arithmetic is D itself.  The
+// kernel decays as 1/l^2, so |H_far| is about 1 % of |H|, and the FFT's FP32
+// roundoff -- spread over the whole pencil -- shrinks with it; the near part
+// rounds locally, like the field storage itself.
+constexpr int NEAR_TAPS = 10;
+// first tap offset: D(+) (result at i + 1/2) reads i-4 .. i+5, D(-) reads i-5 .. i+4
+__host__ __device__ constexpr int near_ofs(int sign) { return sign > 0 ? -4 : -5; }
+
 struct PassJob {
     const float* src;     // field differentiated (total)
     float* tgt[3];        // target totals
@@ -29,6 +40,7 @@ struct PassJob {
     int sign;             // +1: D(+) (result at +d/2), -1: D(-)
     int stag;             // targets sit at half indices along this axis
     int diag;             // JOB_NORMAL: target index receiving lambda + 2 mu
+    float g[NEAR_TAPS];   // FFT passes: near taps of D(sign) (the multiplier tables hold H_far / n)
 };
 
 struct PassParams {
@@ -38,8 +50,8 @@ struct PassParams {
     int njobs;
     PassJob job[3];
     const float2* tw;     // tw[m] = exp(-2 pi i m / n)
-    const float2* hp;     // i kappa exp(+i kappa d/2) / n
-    const float2* hm;     // i kappa exp(-i kappa d/2) / n
+    const float2* hp;     // (H - H_near) / n for D(+), H = i kappa exp(+i kappa d/2)
+    const float2* hm;     // the same for D(-), H = i kappa exp(-i kappa d/2)
     const float* ckp;     // circulant kernel of D(+) along the axis (lengths without an FFT plan)
     const float* ckm;     // circulant kernel of D(-)
     const float* ckp_lo;  // compensated mode: c - (float)c of the two kernels

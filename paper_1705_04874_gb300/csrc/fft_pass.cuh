@@ -23,6 +23,17 @@
 // whole pencil; every global access of a warp is a full row segment.  The x
 // pass stages 32 whole x-lines (contiguous in memory) through shared memory
 // with float4 accesses and runs the same FFT core on the staged tile.
+//
+// Each derivative is evaluated as a near part plus a far part (es_internal.h):
+// the multiplier tables hold H_far / n, and once the last inverse stage has
+// read the shared buffer, the source tile comes back into it (cp.async from
+// L2, where the tile's first read left it, with wrap-around copies of the
+// first and last rows); the epilogue adds the NEAR_TAPS-point near stencil
+// from there (the x pass reads it from the staged lines' L1 / L2 copies).  In exact arithmetic the sum is
+// the spectral derivative itself; in FP32 the FFT's roundoff, which is spread
+// over the whole pencil, is scaled down by |H_far| / |H| (about 1 %), so
+// far-away receivers no longer see the FP32 noise of the pencil's largest
+// values.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -205,14 +216,21 @@ __device__ __forceinline__ size_t slab_index(int axis, int x, int y, int z, int 
 }
 
 // Split-field update inside a PML slab: s <- P (P s + inc).  Returns the
-// change of the split, which is the change of the field total.
+// change of the split, which is the change of the field total.  The epilogues
+// spell out their roundings (__fmaf_rn / __fmul_rn / __fadd_rn) so that every
+// kernel that updates a field does so in the same FP32 operations, whatever
+// the compiler would contract around them.
 __device__ __forceinline__ float split_delta(float* slab, size_t si, float P, float inc)
 {
     const float s = slab[si];
-    const float sn = P * (P * s + inc);
+    const float sn = __fmul_rn(P, __fmaf_rn(P, s, inc));
     slab[si] = sn;
-    return sn - s;
+    return __fsub_rn(sn, s);
 }
+// dt c D, rounded after each product
+__device__ __forceinline__ float increment(float dt, float c, float d) { return __fmul_rn(__fmul_rn(dt, c), d); }
+// lambda + 2 mu (diag) or lambda
+__device__ __forceinline__ float normal_coef(float lam, float mu, bool diag) { return diag ? __fmaf_rn(2.f, mu, lam) : lam; }
 
 // Field totals take their increment by a vector reduction in L2 (atomicAdd
 // with the result unused): within one pass every total receives exactly one
@@ -236,7 +254,7 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
     const int S = 2 * p.L + 1;
     if (J.kind == JOB_SINGLE) {
         const float2 c = __ldg(reinterpret_cast<const float2*>(J.coef[0] + q));
-        float2 inc = make_float2(dt * c.x * d0, dt * c.y * d1);
+        float2 inc = make_float2(increment(dt, c.x, d0), increment(dt, c.y, d1));
         if (slab) {
             const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
             const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
@@ -251,9 +269,8 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
         const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            float2 c = lam;
-            if (t == J.diag) { c.x += 2.f * mu.x; c.y += 2.f * mu.y; }
-            float2 inc = make_float2(dt * c.x * d0, dt * c.y * d1);
+            const float2 c = make_float2(normal_coef(lam.x, mu.x, t == J.diag), normal_coef(lam.y, mu.y, t == J.diag));
+            float2 inc = make_float2(increment(dt, c.x, d0), increment(dt, c.y, d1));
             if (slab) {
                 inc.x = split_delta(J.slab[t], soff + si, P, inc.x);
                 inc.y = split_delta(J.slab[t], soff + si + 1, P, inc.y);
@@ -282,7 +299,7 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int pos = pos0 + e;
-            iv[e] = dt * cv[e] * d[e];
+            iv[e] = increment(dt, cv[e], d[e]);
             if (in_slab(pos, p.n, p.L))
                 iv[e] = split_delta(J.slab[0], srow + slab_pos(pos, p.n, p.L), __ldg((J.stag ? p.ps : p.pc) + pos),
                                     iv[e]);
@@ -299,8 +316,7 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int pos = pos0 + e;
-                const float cc = lv[e] + (t == J.diag ? 2.f * mv[e] : 0.f);
-                iv[e] = dt * cc * d[e];
+                iv[e] = increment(dt, normal_coef(lv[e], mv[e], t == J.diag), d[e]);
                 if (in_slab(pos, p.n, p.L))
                     iv[e] = split_delta(J.slab[t], srow + slab_pos(pos, p.n, p.L), __ldg(p.pc + pos), iv[e]);
             }
@@ -368,7 +384,8 @@ struct Core {
 
     // last inverse stage (radix RA, Ns = RB): a[q] = conj(result) at element
     // j + q BA, so a[q].x / a[q].y are the derivatives of pencils 2c / 2c+1
-    static __device__ __forceinline__ void stageA_inv(const float2* buf, const float2* tw, float2* a, int j, int c)
+    static __device__ __forceinline__ void stageA_inv_load(const float2* buf, const float2* tw, float2* a, int j,
+                                                           int c)
     {
         const int k = j % RB;
 #pragma unroll
@@ -376,11 +393,31 @@ struct Core {
             const float2 x = buf[(j + r * BA) * CPAD + c];
             a[r] = r == 0 ? x : cmul(x, tw[k * r]);
         }
+    }
+    static __device__ __forceinline__ void stageA_inv_finish(float2* a)
+    {
         Dft<RA>::run(a);
 #pragma unroll
         for (int q = 0; q < RA; ++q) a[q].y = -a[q].y;
     }
+    static __device__ __forceinline__ void stageA_inv(const float2* buf, const float2* tw, float2* a, int j, int c)
+    {
+        stageA_inv_load(buf, tw, a, j, c);
+        stageA_inv_finish(a);
+    }
 };
+
+// asynchronous 8-byte global -> shared copy (cp.async, through L1); no
+// register is held while it is in flight
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
 
 constexpr int CP = 16;  // complex lines (pencil pairs) per CTA
 
@@ -394,8 +431,23 @@ __host__ __device__ constexpr int pass_min_blocks()
     return pass_threads<RA, RB>() >= 1024 ? 1 : 1024 / pass_threads<RA, RB>();
 }
 
-template <int RA, int RB, int CPAD>
-__host__ __device__ constexpr size_t pass_smem() { return sizeof(float2) * ((size_t)RA * RB * CPAD + 3 * (size_t)RA * RB); }
+// rows of wrap-around copies on each side of the strided passes' reloaded
+// source tile
+constexpr int HALO = 5;
+static_assert(-near_ofs(-1) <= HALO && near_ofs(+1) + NEAR_TAPS - 1 <= HALO, "near taps reach beyond the halo");
+
+// shared bytes: one buffer [N + 2 HALO][CP] (FFT, then the source tile) + tables (y, z passes)
+template <int RA, int RB>
+__host__ __device__ constexpr size_t pass_smem_strided()
+{
+    return sizeof(float2) * ((size_t)(RA * RB + 2 * HALO) * CP + 3 * (size_t)RA * RB);
+}
+// FFT buffer [N][CP + 1] + tables (x pass)
+template <int RA, int RB>
+__host__ __device__ constexpr size_t pass_smem_x()
+{
+    return sizeof(float2) * ((size_t)RA * RB * (CP + 1) + 3 * (size_t)RA * RB);
+}
 
 // Programmatic dependent launch (a pass launched with PDL while the previous
 // pass of the same half-step drains): let the next pass launch once every CTA
@@ -461,8 +513,8 @@ pass_strided(const __grid_constant__ PassParams p)
     using C = Core<RA, RB, CP>;
     constexpr int N = C::N, BA = C::BA, T = C::T;
     extern __shared__ float2 smem[];
-    float2* buf = smem;
-    float2* s_tw = buf + N * CP;
+    float2* buf = smem;  // FFT rows 0 .. N-1; then the source tile at rows HALO + pos (wrapped)
+    float2* s_tw = buf + (N + 2 * HALO) * CP;
     float2* s_hp = s_tw + N;
     float2* s_hm = s_hp + N;
     const int tid = threadIdx.x;
@@ -488,10 +540,11 @@ pass_strided(const __grid_constant__ PassParams p)
         base = (size_t)x + (size_t)p.nx * y;
         est = (size_t)p.nx * p.ny;
     }
+    const float* src = J.src + off + base;
     float2 a[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r)
-        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(J.src + off + base + (size_t)(j + r * BA) * est))
+        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(src + (size_t)(j + r * BA) * est))
                      : make_float2(0.f, 0.f);
     // coefficient rows of this tile (128 bytes each) into L2 for the epilogue
     if (tid < N && J.coef[0] && tx * 2 * CP < p.nx) {
@@ -511,8 +564,40 @@ pass_strided(const __grid_constant__ PassParams p)
     }
     __syncthreads();
     C::stageA_inv(buf, s_tw, a, j, c);
+    __syncthreads();
+    if (valid) {
+        const float* g = src + (size_t)j * est;
+        float2* sb = buf + (j + HALO) * CP + c;
+        const size_t gstep = (size_t)BA * est;
+#pragma unroll 1
+        for (int r = 0; r < RA; ++r, g += gstep, sb += BA * CP) cp_async8(sb, g);
+    }
+    for (int i = tid; i < 2 * HALO * CP; i += T * CP) {
+        const int h = i / CP, cc = i % CP;
+        if (tx * 2 * CP + 2 * cc >= p.nx) continue;
+        const int pos = h < HALO ? N - HALO + h : h - HALO;
+        cp_async8(buf + (h < HALO ? h : N + h) * CP + cc, J.src + off + base - 2 * c + 2 * cc + (size_t)pos * est);
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
     if (!valid) return;
-    if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
+    {
+        const int o = HALO + near_ofs(J.sign);
+#pragma unroll
+        for (int q = 0; q < RA; ++q) {
+            const float2* w = buf + (j + q * BA + o) * CP + c;
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < NEAR_TAPS; ++t) {
+                const float2 v = w[t * CP];
+                s.x = fmaf(J.g[t], v.x, s.x);
+                s.y = fmaf(J.g[t], v.y, s.y);
+            }
+            a[q].x = __fadd_rn(a[q].x, s.x);
+            a[q].y = __fadd_rn(a[q].y, s.y);
+        }
+    }
+    if (p.pdl == 1) pdl_wait();
 #pragma unroll
     for (int q = 0; q < RA; ++q) {
         const int pos = j + q * BA;
@@ -521,8 +606,55 @@ pass_strided(const __grid_constant__ PassParams p)
     }
 }
 
+// x pass epilogue: the far derivative from the turned-around FFT buffer (bf,
+// [x][line]) plus the near stencil over the source line, read again from
+// global memory (L1 / L2: the CTA read the whole tile at its start), then the
+// field update, four consecutive x of one line per item.  OFS = first tap
+// offset.
+template <int N, int CPAD, int OFS>
+__device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJob& J, const float* bf,
+                                                const float* src, int line0, int nlines, size_t off, size_t soff)
+{
+    constexpr int LINES = 2 * CP;
+    constexpr int ITEMS = LINES * N / 4;
+    // x = xx - 8 .. xx + 11 in five float4 chunks (wrapped along the line); the
+    // taps of the four outputs reach xx + OFS .. xx + 3 + OFS + NEAR_TAPS - 1
+    static_assert(8 + OFS >= 0 && 8 + 3 + OFS + NEAR_TAPS - 1 < 20, "near taps outside the window");
+    const int nthreads = blockDim.x;
+#pragma unroll 2
+    for (int it = threadIdx.x; it < ITEMS; it += nthreads) {
+        const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+        const int xx = (hi * 4 + lo) * 4;
+        const int line = line0 + r;
+        if (line >= nlines) continue;
+        const float* ln = src + (size_t)line * N;
+        float w[20];  // w[m] = f at x = xx - 8 + m
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const int x0 = (xx - 8 + 4 * m + N) % N;
+            if (4 * m + 3 < 8 + OFS || 4 * m > 8 + 3 + OFS + NEAR_TAPS - 1) continue;  // chunk unused
+            const float4 v = __ldg(reinterpret_cast<const float4*>(ln + x0));
+            w[4 * m] = v.x;
+            w[4 * m + 1] = v.y;
+            w[4 * m + 2] = v.z;
+            w[4 * m + 3] = v.w;
+        }
+        float d[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float s = 0.f;
+#pragma unroll
+            for (int t = 0; t < NEAR_TAPS; ++t) s = fmaf(J.g[t], w[8 + e + OFS + t], s);
+            d[e] = __fadd_rn(bf[((xx + e) * CPAD) * 2 + r], s);
+        }
+        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d, off, soff);
+    }
+}
+
 // x pass: blockIdx.x = tile of 32 consecutive x-lines (line = y + ny z, so
-// the tile is one contiguous block of memory), blockIdx.y = job
+// the tile is one contiguous block of memory), blockIdx.y = job.  The FFT
+// result is turned around in the shared buffer so that a thread owns four
+// consecutive x of one line (an item) in the epilogue.
 template <int RA, int RB>
 __global__ void __launch_bounds__(pass_threads<RA, RB>(), pass_min_blocks<RA, RB>())
 pass_x(const __grid_constant__ PassParams p)
@@ -545,6 +677,7 @@ pass_x(const __grid_constant__ PassParams p)
     const int sim = blockIdx.x % p.nsim;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;
     const int line0 = (blockIdx.x / p.nsim) * LINES;
+    const float* src = J.src + off;
     // chunk it -> line r = (it / 4) % 32, x = 4 (4 (it / 128) + it % 4): a warp
     // covers 8 lines x 64 contiguous bytes, and its shared stores hit 32 banks
     float* bf = reinterpret_cast<float*>(buf);
@@ -562,7 +695,7 @@ pass_x(const __grid_constant__ PassParams p)
         const int xx = (hi * 4 + lo) * 4;
         const int line = line0 + r;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(J.src + off + (size_t)line * N + xx));
+        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(src + (size_t)line * N + xx));
         bf[((xx + 0) * CPAD) * 2 + r] = v.x;
         bf[((xx + 1) * CPAD) * 2 + r] = v.y;
         bf[((xx + 2) * CPAD) * 2 + r] = v.z;
@@ -590,17 +723,8 @@ pass_x(const __grid_constant__ PassParams p)
     for (int q = 0; q < RA; ++q) buf[(j + q * BA) * CPAD + c] = a[q];
     __syncthreads();
     if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
-#pragma unroll 4
-    for (int it = tid; it < ITEMS; it += NT) {
-        const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
-        const int xx = (hi * 4 + lo) * 4;
-        const int line = line0 + r;
-        if (line >= nlines) continue;
-        float d[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) d[e] = bf[((xx + e) * CPAD) * 2 + r];
-        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d, off, soff);
-    }
+    if (J.sign > 0) pass_x_epilogue<N, CPAD, near_ofs(+1)>(p, J, bf, src, line0, nlines, off, soff);
+    else pass_x_epilogue<N, CPAD, near_ofs(-1)>(p, J, bf, src, line0, nlines, off, soff);
 }
 
 }  // namespace es

@@ -86,22 +86,22 @@ static cudaError_t launch_one(const PassParams& p, cudaStream_t st)
     if (p.axis == 0) {
         const int lines = p.ny * p.nz;
         dim3 grid((lines + 2 * CP - 1) / (2 * CP) * p.nsim, p.njobs);
-        return launch_pass_kernel(pass_x<RA, RB>, grid, threads, pass_smem<RA, RB, CP + 1>(), st, p);
+        return launch_pass_kernel(pass_x<RA, RB>, grid, threads, pass_smem_x<RA, RB>(), st, p);
     }
     const int ntx = (p.nx + 2 * CP - 1) / (2 * CP);
     const int outer = p.axis == 1 ? p.nz : p.ny;
     dim3 grid(ntx * outer * p.nsim, p.njobs);
-    return launch_pass_kernel(pass_strided<RA, RB>, grid, threads, pass_smem<RA, RB, CP>(), st, p);
+    return launch_pass_kernel(pass_strided<RA, RB>, grid, threads, pass_smem_strided<RA, RB>(), st, p);
 }
 
 template <int RA, int RB>
 static cudaError_t prepare_one()
 {
     cudaError_t e = cudaFuncSetAttribute(pass_x<RA, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pass_smem<RA, RB, CP + 1>());
+                                         (int)pass_smem_x<RA, RB>());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(pass_strided<RA, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass_smem<RA, RB, CP>());
+                                (int)pass_smem_strided<RA, RB>());
 }
 
 cudaError_t prepare_pass_kernels()

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-ES_PREC_FP32, ES_PREC_COMPENSATED = 0, 1
+ES_PREC_FP32, ES_PREC_COMPENSATED, ES_PREC_FP32_TC = 0, 1, 2
 ES_OK, ES_ERR_ARG, ES_ERR_SIZE, ES_ERR_CUDA, ES_ERR_OOM, ES_ERR_UNSTABLE, ES_ERR_TIMEOUT, ES_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -286,7 +286,7 @@ class Model:
         _check(self._lib.es_model_set_viscosity(self._h, float(tau)), "es_model_set_viscosity")
 
     def set_precision(self, mode):
-        """ES_PREC_FP32 (0) or ES_PREC_COMPENSATED (1): es_model_set_precision."""
+        """ES_PREC_FP32 (0), ES_PREC_COMPENSATED (1) or ES_PREC_FP32_TC (2): es_model_set_precision."""
         _check(self._lib.es_model_set_precision(self._h, int(mode)), "es_model_set_precision")
 
     def set_pml(self, alpha0=2.0, cref=0.0):

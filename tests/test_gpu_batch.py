@@ -49,7 +49,7 @@ def test_batch_equals_single_runs(es, orc):
     # and the first simulation against the oracle
     ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml,
                        sources=[dict(kind="moment", pos=pos[0], m=mts[0], w=wav[0])], receivers=rcv)["traces"]
-    assert np.median(trace_errors(batched[0], ref)) < 1e-4
+    assert trace_errors(batched[0], ref).max() < 1e-4
 
 
 def test_batch_back_to_single_and_resize(es):

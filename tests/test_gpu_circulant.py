@@ -77,16 +77,19 @@ def test_all_odd_grid_run_matches_oracle(es, orc):
 
 def test_mixed_fft_and_circulant_axes(es, orc):
     """48 x 32 x 30 marine model: x and y through the FFT passes, z (30)
-    through the circulant pass; double couple, 5-cell PML, 100 steps."""
+    through the circulant pass; explosive source, 5-cell PML, 100 steps.  (With
+    a double couple, two seabed pressure traces lie on its nodal planes at 1e-3
+    of the largest, where FP32 storage of the fields alone -- exact FP64
+    derivatives, FP32 state -- already differs from the oracle by 9.8e-5.)"""
     rho, cp, cs = synth.marine_model(shape=(30, 32, 48), seed=2)
     nt = 100
     dt = cfl_dt(cp, 10.0)
     w = synth.ricker(nt, dt, 30.0)
     rcv = orc.seabed_receivers(cs, 5, 4, 4)
-    src = [dict(kind="moment", pos=(24, 16, 18), m=synth.double_couple_sdr(30, 60, 90), w=w)]
+    src = [dict(kind="moment", pos=(24, 16, 18), m=synth.explosive(), w=w)]
     gpu, state, ref = _run_both(es, orc, rho, cp, cs, pml=5, nt=nt, sources=src, rcv=rcv)
     err = trace_errors(gpu, ref["traces"])
-    assert np.median(err) < TOL and err.max() < 1e-3, (np.median(err), err.max())
+    assert err.max() < TOL, (np.median(err), err.max())
     for f in range(9):
         assert rel_l2(state[f], ref["state"][f]) < TOL, f
 
@@ -154,13 +157,14 @@ def test_compensated_run_with_a_long_circulant_axis(es, orc):
 @pytest.mark.parametrize("shape,pml,nb", [((200, 16, 32), 3, 1), ((193, 12, 20), 3, 1), ((301, 12, 24), 4, 2),
                                           ((512, 4, 8), 0, 1), ((16, 200, 24), 3, 1), ((12, 12, 201), 3, 1)])
 def test_tensor_core_passes_match_oracle(es, orc, shape, pml, nb):
-    """Axes of 192 to 512 cells without an FFT plan run their passes on the
-    tensor cores in FP32 mode (field and kernel split in three BF16 parts,
-    six products, FP32 accumulation; the update in a separate kernel): the
-    first simulation against the oracle (median trace error below 1e-4, every
-    field within 1e-4), the others of a batch equal to single-source runs bit
-    for bit.  Long z axes (the shortest such, 193, and the longest, 512, no
-    PML), a long y axis and a long odd x axis, with the PML along each."""
+    """With ES_PREC_FP32_TC, axes of 192 to 512 cells without an FFT plan run
+    their passes on the tensor cores (the far part of the kernel matrix and the
+    field split in three BF16 parts each, six products, FP32 accumulation; the
+    near stencil and the update in a separate kernel): the first simulation
+    against the oracle (every trace and every field within 1e-4), the others
+    of a batch equal to single-source runs bit for bit.  Long z axes (the
+    shortest such, 193, and the longest, 512, no PML), a long y axis and a
+    long odd x axis, with the PML along each."""
     rho, cp, cs = synth.marine_model(shape=shape, seed=sum(shape))
     nt = 60
     dt = cfl_dt(cp, 10.0)
@@ -170,7 +174,9 @@ def test_tensor_core_passes_match_oracle(es, orc, shape, pml, nb):
     mts = np.array([synth.random_dc(rng) for _ in range(nb)])
     wav = np.stack([synth.ricker(nt, dt, 30.0)] * nb)
     with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
-        assert m.kernels_per_step() == 10  # two field-update kernels for the two z passes
+        assert m.kernels_per_step() == 8  # the CUDA-core circulant passes by default
+        m.set_precision(es.ES_PREC_FP32_TC)
+        assert m.kernels_per_step() == 10  # two field-update kernels for the two tensor-core passes
         rcv = np.array([[x, y, 3] for x in range(0, shape[2], max(1, shape[2] // 4))
                         for y in range(0, shape[1], max(1, shape[1] // 3))], np.int32)
         if nb == 1:
@@ -185,10 +191,11 @@ def test_tensor_core_passes_match_oracle(es, orc, shape, pml, nb):
                        sources=[dict(kind="moment", pos=pos[0], m=mts[0], w=wav[0])], receivers=rcv,
                        state=np.zeros((9,) + rho.shape))
     err = trace_errors(gpu[0], ref["traces"])
-    assert np.median(err) < TOL and err.max() < 1e-3, (np.median(err), err.max())
+    assert err.max() < TOL, (np.median(err), err.max())
     for f in range(9):
         assert rel_l2(st0[f], ref["state"][f]) < TOL, f
     for b in range(1, nb):
         with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m1:
+            m1.set_precision(es.ES_PREC_FP32_TC)
             m1.source_set(pos[b], mts[b], wav[b])
             assert np.array_equal(m1.run(nt, dt, rcv), gpu[b]), b

@@ -2,10 +2,11 @@
 benchmark times (es_run and es_run_group through the C ABI): 128^3 and 256^3
 marine models, and the batched group of 64 + 16 + 8 sources on 128^3, 96^3
 and 160^3.
-The oracle cannot run thousands of steps at these sizes in a test, so the
-whole field state is compared after a few steps, and properties that hold at
-any length (exact linearity and delay, receiver maps, energy conservation with
-the PML off) are checked over longer runs on the GPU alone."""
+Every trace of the 128^3 configuration over its full 2000 steps and of the
+256^3 configuration over its first 400 steps against the oracle; whole field
+states after a few steps; and properties that hold at any length (exact
+linearity and delay, receiver maps, energy conservation with the PML off) over
+longer runs on the GPU alone."""
 import numpy as np
 import pytest
 
@@ -58,6 +59,40 @@ def test_marine_256_field_parity(es, orc):
     _field_parity(es, orc, 256, 12, mt, 10, 1, 64)
 
 
+def _bench_trace_parity(es, orc, name, nt):
+    """Every trace of a benchmarked configuration (bench.py's own inputs and
+    receivers, es_run as the benchmark calls it) against the oracle, per
+    trace within 1e-4 (floor 1e-3 of the component's largest trace)."""
+    import bench
+    w = bench.workload(name)
+    inp = bench.build_inputs(w)
+    with es.Model(inp["rho"], inp["cp"], inp["cs"], dx=10.0, pml=w["pml"]) as m:
+        rcv = m.seabed_receivers(w["rx"], w["rx"])
+        m.source_set(inp["pos"], inp["mt"], inp["wav"][:nt])
+        gpu = m.run(nt, inp["dt"], rcv)
+    ref = orc.simulate(inp["rho"], inp["cp"], inp["cs"], dx=10.0, dt=inp["dt"], nt=nt, pml=w["pml"],
+                       sources=[dict(kind="moment", pos=inp["pos"], m=inp["mt"], w=inp["wav"][:nt])],
+                       receivers=rcv)["traces"]
+    err = trace_errors(gpu, ref)
+    assert err.max() < 1e-4, (np.median(err), err.max())
+    return err
+
+
+def test_c2_traces_full_length(es, orc):
+    """The 128^3 benchmark configuration (marine model, PML 10, DC strike 30
+    dip 60 rake 90, Ricker 30 Hz, 32 x 32 seabed receivers) for all 2000
+    steps: all 1024 4C traces (about 200 s of oracle time on 16 cores)."""
+    _bench_trace_parity(es, orc, "128", 2000)
+
+
+def test_c3_traces_first_400_steps(es, orc):
+    """The 256^3 benchmark configuration (PML 12, random double couple in the
+    reservoir box, 64 x 64 seabed receivers) for its first 400 steps, by which
+    the P and S arrivals have crossed the seabed: all 4096 4C traces (about
+    360 s of oracle time on 16 cores)."""
+    _bench_trace_parity(es, orc, "256", 400)
+
+
 def test_marine_256_linearity_over_many_steps(es):
     n, pml, nt = 256, 12, 400
     rho, cp, cs = synth.marine_model(n, seed=1)
@@ -78,7 +113,17 @@ def test_marine_256_linearity_over_many_steps(es):
         m.source_set(pos, mt, np.concatenate([np.zeros(k, np.float32), w])[:nt])
         c = m.run(nt, dt, rcv)
     assert np.abs(a).max() > 0
-    assert np.array_equal(b, 2 * a)
+    # Doubling the source doubles every operation's result exactly in binary
+    # floating point, except where an intermediate falls below FP32's normal
+    # range (2^-126), where rounding is absolute: the spectral derivative
+    # reaches every cell after the first step, so the earliest samples far
+    # from the source pass through such values.  Bit-exact wherever the trace
+    # is above 2^-90; below it, equal to within 2^-100.
+    big = np.abs(a) >= 2.0 ** -90
+    assert big.sum() > 0.9 * a.size
+    assert np.array_equal(b[big], 2 * a[big])
+    assert np.abs(b.astype(np.float64) - 2 * a.astype(np.float64)).max() <= 2.0 ** -100
+    # a delayed source repeats the same operations on the same values: exact
     assert np.array_equal(c[..., k:], a[..., :nt - k])
 
 
@@ -165,4 +210,4 @@ def test_batched_group_full_size(es, orc):
     ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dts[1], nt=nt, pml=pml,
                        sources=[dict(kind="moment", pos=pos[0], m=mts[0], w=wav[0])], receivers=rcvs[1])["traces"]
     err = trace_errors(got[1][0], ref)
-    assert np.median(err) < 1e-4 and err.max() < 1e-3, (np.median(err), err.max())
+    assert err.max() < 1e-4, (np.median(err), err.max())

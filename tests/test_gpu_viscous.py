@@ -32,9 +32,8 @@ def _setup(shape=(32, 40, 48), seed=3, nt=120):
 
 @pytest.mark.parametrize("r,prec", [(0.1, 0), (0.2, 0), (0.1, 1)])
 def test_viscous_run_matches_oracle(es, orc, r, prec):
-    """FP32 derivatives: the median trace within 1e-4 and the far traces at the
-    FP32 floor of a heterogeneous run (as for the elastic runs); compensated
-    derivatives (es_model_set_precision): every trace within 1e-4."""
+    """FP32 and compensated derivatives (es_model_set_precision): every trace
+    and every field within 1e-4."""
     rho, cp, cs, dt, w = _setup()
     nt, pml = len(w), 4
     src = [dict(kind="moment", pos=(24, 20, 14), m=synth.double_couple_sdr(20, 70, 110), w=w)]
@@ -50,10 +49,7 @@ def test_viscous_run_matches_oracle(es, orc, r, prec):
     ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=pml, sources=src, receivers=rcv,
                        state=np.zeros((9,) + rho.shape), tau=r * dt)
     err = trace_errors(gpu, ref["traces"])
-    if prec:
-        assert err.max() < TOL, err.max()
-    else:
-        assert np.median(err) < TOL and err.max() < 5e-3, (np.median(err), err.max())
+    assert err.max() < TOL, (np.median(err), err.max())
     for f in range(9):
         assert rel_l2(st[f], ref["state"][f]) < TOL, f
     # and it differs from the elastic run by far more than the tolerance
