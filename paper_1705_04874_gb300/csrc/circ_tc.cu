@@ -354,14 +354,18 @@ __global__ void circ_tc_update_xy_kernel(const __grid_constant__ PassParams p)
             const int pos = p.axis == 0 ? (int)x : (int)(line % p.ny);
             const size_t base = p.axis == 0 ? (size_t)line * p.nx : (size_t)q - (size_t)pos * p.nx;
             const size_t est = p.axis == 0 ? 1 : (size_t)p.nx;
-            float s = dv[k];
+            float v[NEAR_TAPS];
 #pragma unroll
             for (int t = 0; t < NEAR_TAPS; ++t) {
                 int i = pos + ofs + t;
                 i += i < 0 ? p.n : 0;
                 i -= i >= p.n ? p.n : 0;
-                s = fmaf(J.g[t], __ldg(f + base + (size_t)i * est), s);
+                v[t] = __ldg(f + base + (size_t)i * est);
             }
+            float s = 0.f;
+#pragma unroll
+            for (int t = 0; t < NEAR_PAIRS; ++t) s = __fmaf_rn(J.g[t], __fsub_rn(v[t], v[NEAR_TAPS - 1 - t]), s);
+            s = __fadd_rn(dv[k], s);
             if (p.axis == 0)
                 update_cell(p, J, q, (int)x, (int)x, (int)line, 0, s, off, soff);
             else
@@ -385,7 +389,7 @@ __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
     const float* f = J.src + off + pxy;
     const int z0 = blockIdx.y * UPD_Z;
     const int ofs = near_ofs(J.sign);
-    float dv[UPD_Z];
+    float dv[UPD_Z], v[UPD_Z + NEAR_TAPS - 1];
 #pragma unroll
     for (int k = 0; k < UPD_Z; ++k) dv[k] = z0 + k < p.n ? d[(size_t)pxy + (size_t)(z0 + k) * P] : 0.f;
 #pragma unroll
@@ -393,12 +397,14 @@ __global__ void circ_tc_update_kernel(const __grid_constant__ PassParams p)
         int i = z0 + ofs + m;
         i += i < 0 ? p.n : 0;
         i -= i >= p.n ? p.n : 0;
-        const float v = __ldg(f + (size_t)i * P);
+        v[m] = __ldg(f + (size_t)i * P);
+    }
 #pragma unroll
-        for (int k = 0; k < UPD_Z; ++k) {
-            const int t = m - k;
-            if (t >= 0 && t < NEAR_TAPS) dv[k] = fmaf(J.g[t], v, dv[k]);
-        }
+    for (int k = 0; k < UPD_Z; ++k) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < NEAR_PAIRS; ++t) s = __fmaf_rn(J.g[t], __fsub_rn(v[k + t], v[k + NEAR_TAPS - 1 - t]), s);
+        dv[k] = __fadd_rn(dv[k], s);
     }
 #pragma unroll
     for (int k = 0; k < UPD_Z; ++k)

@@ -212,11 +212,19 @@ void axis_tables(int n, double d, std::vector<float2>& tw, std::vector<float2>& 
         float* g = s == 0 ? gp : gm;
         const int ofs = near_ofs(s == 0 ? +1 : -1);
         std::vector<double> nr(n, 0.0), ni(n, 0.0);  // H_near / n
+        // the taps in antisymmetric pairs, g[NEAR_TAPS - 1 - t] = -g[t] (exact for the staggered
+        // kernel up to FP64 roundoff; enforced here so the passes can sum differences)
+        for (int t = 0; t < NEAR_PAIRS; ++t) {
+            g[t] = g[NEAR_TAPS - 1 - t] = 0.f;
+            if (n <= NEAR_TAPS) continue;
+            const double lo = kernel_entry(s, ((-(ofs + t)) % n + n) % n);  // (D f)_i = sum_l c_l f_{i - l}
+            const double hi = kernel_entry(s, ((-(ofs + NEAR_TAPS - 1 - t)) % n + n) % n);
+            g[t] = (float)(0.5 * (lo - hi));
+            g[NEAR_TAPS - 1 - t] = -g[t];
+        }
         for (int t = 0; t < NEAR_TAPS; ++t) {
-            g[t] = 0.f;
             if (n <= NEAR_TAPS) continue;
             const int delta = ofs + t;                      // (N f)_i gains g_t f_{i + delta}
-            g[t] = (float)kernel_entry(s, ((-delta) % n + n) % n);  // (D f)_i = sum_l c_l f_{i - l}
             for (int m = 0; m < n; ++m) {
                 const long long md = (((long long)m * delta) % n + n) % n;
                 const double a = 2.0 * pi * (double)md / (double)n;

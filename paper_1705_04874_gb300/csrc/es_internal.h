@@ -28,7 +28,10 @@ enum JobKind {
 // roundoff -- spread over the whole pencil -- shrinks with it; the near part
 // rounds locally, like the field storage itself.
 constexpr int NEAR_TAPS = 10;
-// first tap offset: D(+) (result at i + 1/2) reads i-4 .. i+5, D(-) reads i-5 .. i+4
+// The kernel is antisymmetric about the staggered point, g[NEAR_TAPS - 1 - t] = -g[t],
+// so N f = sum over t < NEAR_PAIRS of g_t (f_{i+o+t} - f_{i+o+NEAR_TAPS-1-t}).
+constexpr int NEAR_PAIRS = NEAR_TAPS / 2;
+// first tap offset o: D(+) (result at i + 1/2) reads i-4 .. i+5, D(-) reads i-5 .. i+4
 __host__ __device__ constexpr int near_ofs(int sign) { return sign > 0 ? -4 : -5; }
 
 struct PassJob {
