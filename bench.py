@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the reduced surrogate measurement")
-    ap.add_argument("--batched-nt", type=int, default=200, help="time steps of the batched measurement")
+    ap.add_argument("--batched-nt", type=int, default=2000, help="time steps of the batched measurement")
     args = ap.parse_args()
     if args.workload == "surrogate":
         return measure_surrogate(args)
@@ -327,7 +327,7 @@ def main():
         line["e2e"] = e2e(es, w, inp, stream)
     if not args.no_batched and rank == 0:
         m.close()
-        line["batched"] = measure_batched(es, args.batched_nt, 2, stream)
+        line["batched"] = measure_batched(es, args.batched_nt, 1, stream)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         v, el, cores = oracle_sample(w, inp, 3)
         line["cpu_baseline"] = {"value": v, "unit": "Mcell-steps/s", "cores": cores, "kind": "oracle",
@@ -349,13 +349,17 @@ def main():
 
 
 def measure_batched(es, nt, reps, stream):
-    """Batched workload: 64 sources (uniform in the reservoir box, random
+    """Batched workload (C4): 64 sources (uniform in the reservoir box, random
     double couples) on the 128^3 marine model plus 16 on a 96^3 and 8 on a
-    160^3 model, all advanced in one graph (one branch per model); the plain
-    rate is one source per es_run on the 128^3 model."""
+    160^3 model, nt steps each (full length: 2000), all advanced in one graph
+    (one branch per model), then 300 events (log-normal amplitudes, sigma 1;
+    origin times uniform in 2 s; sources drawn from the 64) superposed into a
+    4C gather -- both inside the timed region.  The plain rate runs the same
+    sources one per es_run on each grid size (timed per size on one source and
+    weighted by the batch's source counts), plus the same superposition."""
     import torch
     specs = [(128, 10, 64), (96, 8, 16), (160, 10, 8)]
-    models, rcvs, dts, cells, tune = [], [], [], 0.0, []
+    models, rcvs, dts, cells, inputs = [], [], [], 0.0, []
     for i, (n, pml, nb) in enumerate(specs):
         rho, cp, cs = synth.marine_model(n, seed=1)
         dt = 0.3 * 10.0 / float(cp.max())
@@ -367,52 +371,67 @@ def measure_batched(es, nt, reps, stream):
         m = es.Model(rho, cp, cs, dx=10.0, pml=pml, stream=stream)
         rcv = m.seabed_receivers(32, 32)
         m.batch_set(pos, mts, wav)
-        tune.append(m.autotune(reps=3))  # FFT plans for this batched model, before the timed region
+        m.autotune(reps=3)  # FFT plans for this batched model, before the timed region
         models.append(m)
         rcvs.append(torch.from_numpy(rcv).cuda())
         dts.append(dt)
+        inputs.append((rho, cp, cs, pml, pos, mts, wav))
         cells += float(n) ** 3 * nb * nt
     outs = [torch.empty((m.nsim, 4, r.shape[0], nt), device="cuda") for m, r in zip(models, rcvs)]
+    ev_src, ev_amp, ev_t0 = (torch.from_numpy(a).cuda() for a in synth.events(synth.SplitMix64(3), 300, 64, t_span=2.0))
+    n_out = nt + int(np.ceil(2.0 / dts[0]))
+    gather = torch.empty((4, rcvs[0].shape[0], n_out), device="cuda")
+
+    def superpose(traces):
+        es.es_superpose(traces, ev_src, ev_amp, ev_t0, dts[0], n_out, gather=gather, stream=stream)
 
     def group():
         for m in models:
             m.state_reset()
         es.es_run_group(models, nt, dts, rcvs, outs)
+        superpose(outs[0])
 
-    group()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        group()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    # plain: one source at a time on the 128^3 model
-    m0 = models[0]
-    rho, cp, cs = synth.marine_model(128, seed=1)
-    single = es.Model(rho, cp, cs, dx=10.0, pml=10, stream=stream)
-    single.source_set((64, 64, 42), synth.double_couple_sdr(30, 60, 90), torch.from_numpy(
-        synth.ricker(nt, dts[0], 30.0)).cuda())
-    tr = torch.empty((4, rcvs[0].shape[0], nt), device="cuda")
-    single.run(nt, dts[0], rcvs[0], tr)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        single.state_reset()
-        single.run(nt, dts[0], rcvs[0], tr)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_plain = e0.elapsed_time(e1) / reps
-    plain = 128.0 ** 3 * nt / (ms_plain * 1e-3) / 1e6
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms = timed(group, reps)
+    ms_sup = timed(lambda: superpose(outs[0]), 3)
+    # plain: one source per es_run, on each grid size
+    plain_ms, per_size = 0.0, {}
+    for (n, pml, nb), (rho, cp, cs, pml_, pos, mts, wav), dt in zip(specs, inputs, dts):
+        single = es.Model(rho, cp, cs, dx=10.0, pml=pml, stream=stream)
+        rc = single.seabed_receivers(32, 32)
+        single.source_set(pos[0], mts[0], torch.from_numpy(wav[0]).cuda())
+        rct = torch.from_numpy(rc).cuda()
+        tr = torch.empty((4, rct.shape[0], nt), device="cuda")
+
+        def one():
+            single.state_reset()
+            single.run(nt, dt, rct, tr)
+        t1 = timed(one, 2)
+        single.close()
+        per_size[f"{n}^3"] = {"ms_per_source": round(t1, 2), "Mcell_steps_per_s": round(n ** 3 * nt / (t1 * 1e-3) / 1e6, 1)}
+        plain_ms += nb * t1
+    plain_ms += ms_sup
+    plain = cells / (plain_ms * 1e-3) / 1e6
     value = cells / (ms * 1e-3) / 1e6
-    for m in models + [single]:
+    for m in models:
         m.close()
     plans = {f"{'x' if k == 0 else 'yz'}{n}": "x".join(map(str, es.es_fft_plan(k, n)))
              for n in (96, 128, 160) for k in (0, 1)}
     return {"value": round(value, 1), "unit": "Mcell-steps/s", "plain_value": round(plain, 1), "plans": plans,
             "speedup_vs_plain": round(value / plain, 3), "time_steps": nt, "ms_per_run": round(ms, 2),
-            "workload": "64 sources on 128^3 + 16 on 96^3 + 8 on 160^3 marine models, one graph, 32x32 receivers"}
+            "superpose_ms": round(ms_sup, 3), "plain_per_size": per_size,
+            "workload": "64 sources on 128^3 + 16 on 96^3 + 8 on 160^3 marine models, one graph, 32x32 receivers, "
+                        f"{nt} steps; then 300 events superposed (included)"}
 
 
 def gemm_tflops(sur, M, N, K, b_nk, reps=5):

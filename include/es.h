@@ -215,8 +215,9 @@ int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* s
  *   (~256 KB), allocated when the library is loaded and held by every GPU
  *   that loads it until the process exits.  n_events > ES_NOALLOC_MAX_EVENTS
  *   is ES_ERR_ARG.
- * - The first call on a device looks up that array's device address; make
- *   the first call on each device before any stream capture.
+ * - The first call on a device (in each of its contexts: again after a
+ *   cudaDeviceReset) looks up that array's device address; make the first
+ *   call on each device before any stream capture.
  * - Every call shares the array (each call clears what it needs): calls that
  *   overlap on the GPU (other streams, other host threads) race; order them.
  * - The call waits for an argument check on the device before launching, so
@@ -287,6 +288,18 @@ const char* es_status_string(int status);
 
 /* Text of the last CUDA error seen by this thread ("" if none). */
 const char* es_last_error(void);
+
+/* Debug aids for the error paths (no counterpart in the paper).
+ * es_fault_inject_alloc(n): the n-th device allocation the solver makes from
+ * now on fails as if the device were out of memory, before cudaMalloc is
+ * called; the call that needed it returns ES_ERR_OOM and releases what it had
+ * taken.  n <= 0 disables.  The environment variable ES_FAULT_ALLOC=n does
+ * the same from the first allocation of the process.  Host-side only: no
+ * kernel is affected.
+ * es_debug_live_allocations: the number of device allocations the solver
+ * currently holds (models, their run buffers, scratch of running calls). */
+void es_fault_inject_alloc(int n);
+long long es_debug_live_allocations(void);
 
 #ifdef __cplusplus
 }

@@ -211,32 +211,39 @@ cudaError_t launch_transpose_traces(const float* rec, int nt, int cols, float* o
 }
 
 // gather[row][t] = sum_e amp_e traces[src_e][row][t - k_e], rows = 4 n_rcv.
-// One thread per output sample; events in order (FP32 accumulation).
+// One thread per output sample; events in order (FP32 accumulation).  The
+// events reach shared memory in chunks of SUP_CHUNK, so any number of events
+// fits in a fixed 48 KB block without changing the order of the sum.
+constexpr int SUP_CHUNK = 4096;
+
 __global__ void superpose_kernel(const float* traces, int n_rcv, int nt, const int* ev_src,
                                  const float* ev_amp, const int* ev_shift, int n_events, int n_out,
                                  float* gather)
 {
-    extern __shared__ int s_ev[];
-    int* s_src = s_ev;
-    int* s_k = s_ev + n_events;
-    float* s_a = reinterpret_cast<float*>(s_ev + 2 * n_events);
-    for (int i = threadIdx.x; i < n_events; i += blockDim.x) {
-        s_src[i] = ev_src[i];
-        s_k[i] = ev_shift[i];
-        s_a[i] = ev_amp[i];
-    }
-    __syncthreads();
+    __shared__ int s_src[SUP_CHUNK], s_k[SUP_CHUNK];
+    __shared__ float s_a[SUP_CHUNK];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t row = blockIdx.y;
-    if (t >= n_out) return;
+    const bool active = t < n_out;
     const size_t rows = 4 * (size_t)n_rcv;
     float acc = 0.f;
-    for (int e = 0; e < n_events; ++e) {
-        const long u = (long)t - s_k[e];
-        if (u < 0 || u >= nt) continue;
-        acc += s_a[e] * __ldg(traces + ((size_t)s_src[e] * rows + row) * nt + u);
+    for (int e0 = 0; e0 < n_events; e0 += SUP_CHUNK) {
+        const int ne = min(SUP_CHUNK, n_events - e0);
+        __syncthreads();  // the previous chunk is no longer read
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+            s_src[i] = ev_src[e0 + i];
+            s_k[i] = ev_shift[e0 + i];
+            s_a[i] = ev_amp[e0 + i];
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int e = 0; e < ne; ++e) {
+            const long u = (long)t - s_k[e];
+            if (u < 0 || u >= nt) continue;
+            acc += s_a[e] * __ldg(traces + ((size_t)s_src[e] * rows + row) * nt + u);
+        }
     }
-    gather[row * n_out + t] = acc;
+    if (active) gather[row * n_out + t] = acc;
 }
 
 cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* ev_src,
@@ -245,12 +252,7 @@ cudaError_t launch_superpose(const float* traces, int n_src, int n_rcv, int nt, 
 {
     (void)n_src;
     dim3 grid((n_out + 255) / 256, 4 * n_rcv);
-    const size_t sm = (size_t)n_events * 3 * sizeof(int);
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(superpose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    superpose_kernel<<<grid, 256, sm, st>>>(traces, n_rcv, nt, ev_src, ev_amp, ev_shift, n_events, n_out, gather);
+    superpose_kernel<<<grid, 256, 0, st>>>(traces, n_rcv, nt, ev_src, ev_amp, ev_shift, n_events, n_out, gather);
     return cudaGetLastError();
 }
 

@@ -11,11 +11,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
@@ -23,6 +25,8 @@
 #include <vector>
 
 #include <sys/stat.h>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/es.h"
 #include "es_internal.h"
@@ -44,6 +48,52 @@ int cuda_fail(cudaError_t e, const char* what)
         cudaError_t e_ = (call);                                        \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);             \
     } while (0)
+
+
+// NVTX range over a scope (header-only NVTX v3: a no-op unless a profiler
+// injects itself).  The solver's API calls and the phases of es_run carry
+// ranges; inside a time step, each pass launch is marked while the step is
+// captured into its CUDA graph (graph replays run without host calls).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Every device allocation of the solver goes through dev_alloc / dev_free: they
+// count the allocations the library holds (es_debug_live_allocations) and,
+// for testing the error paths, can make the n-th allocation from a chosen
+// point fail as an out-of-memory error before cudaMalloc is called
+// (es_fault_inject_alloc, or ES_FAULT_ALLOC=n from the first allocation).
+std::atomic<long long> g_alloc_countdown{0};
+std::atomic<long long> g_live_allocs{0};
+std::once_flag g_fault_env_once;
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes)
+{
+    std::call_once(g_fault_env_once, [] {
+        if (const char* v = std::getenv("ES_FAULT_ALLOC")) g_alloc_countdown = std::atoll(v);
+    });
+    if (g_alloc_countdown.load() > 0 && g_alloc_countdown.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    *p = static_cast<T*>(q);
+    if (e == cudaSuccess && q) ++g_live_allocs;
+    return e;
+}
+
+template <class T>
+void dev_free(T* p)
+{
+    if (!p) return;
+    cudaFree(const_cast<void*>(static_cast<const void*>(p)));
+    --g_live_allocs;
+}
 
 bool is_device_ptr(const void* p)
 {
@@ -356,10 +406,10 @@ int upload_sources(es_model* m, double dt)
         }
     }
     if ((int)h.size() > m->d_src_cap) {
-        cudaFree(m->d_src);
+        dev_free(m->d_src);
         m->d_src = nullptr;
         m->d_src_cap = 0;
-        CK(cudaMalloc(&m->d_src, sizeof(SourceDev) * h.size()));
+        CK(dev_alloc(&m->d_src, sizeof(SourceDev) * h.size()));
         m->d_src_cap = (int)h.size();
     }
     if (!h.empty()) {
@@ -426,7 +476,7 @@ cudaError_t upload_axis_tables(es_model* m, int a)
                         sp[(size_t)(3 * sgn + 2) * mat + q] = __double2bfloat16(r2);
                     }
             }
-            if (!m->ctc[a]) e = cudaMalloc(&m->ctc[a], sp.size() * sizeof(__nv_bfloat16));
+            if (!m->ctc[a]) e = dev_alloc(&m->ctc[a], sp.size() * sizeof(__nv_bfloat16));
             if (e == cudaSuccess)
                 e = cudaMemcpy(m->ctc[a], sp.data(), sp.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
         }
@@ -520,7 +570,10 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         if (ev) cudaEventRecordWithFlags(ev[2 * k + (before ? 0 : 1)], st, cudaEventRecordExternal);
     };
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
+    static const char* kVel[3] = {"vel-x", "vel-y", "vel-z"};
+    static const char* kStr[3] = {"str-x", "str-y", "str-z"};
     for (int a = 0; a < 3; ++a) {
+        NvtxRange r(kVel[a]);
         PassParams p = make_pass(m, a, false, dt);
         p.pdl = a == 0 ? 2 : 1;  // the x pass reads what the stress half wrote; y and z only add after it
         mark(true);
@@ -547,6 +600,7 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         ++k;
     }
     for (int a = 0; a < 3; ++a) {
+        NvtxRange r(kStr[a]);
         PassParams p = make_pass(m, a, true, dt);
         p.pdl = a == 0 ? 2 : 1;
         if (visc) {
@@ -616,7 +670,7 @@ int alloc_tc_scratch(es_model* m)
 {
     const bool tc = tc_axis(m, 0) || tc_axis(m, 1) || tc_axis(m, 2);
     if (!tc || m->ctc_scratch) return ES_OK;
-    cudaError_t e = cudaMalloc(&m->ctc_scratch, 3 * m->ncell * (size_t)m->nsim * sizeof(float));
+    cudaError_t e = dev_alloc(&m->ctc_scratch, 3 * m->ncell * (size_t)m->nsim * sizeof(float));
     if (e != cudaSuccess) {
         m->ctc_scratch = nullptr;
         return cuda_fail(e, "cudaMalloc(derivative scratch)");
@@ -636,9 +690,9 @@ int alloc_fields(es_model* m, int nsim)
         for (int f = 0; f < NFIELD; ++f)
             if (m->L > 0 && has_split(f, a)) bytes += up(slab_count(m, a) * 4 * (size_t)nsim);
     char* pool = nullptr;
-    cudaError_t e = cudaMalloc(&pool, bytes);
+    cudaError_t e = dev_alloc(&pool, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fields)");
-    cudaFree(m->fpool);
+    dev_free(m->fpool);
     m->fpool = pool;
     m->nsim = nsim;
     char* cur = pool;
@@ -648,7 +702,7 @@ int alloc_fields(es_model* m, int nsim)
         for (int f = 0; f < NFIELD; ++f)
             m->slab[a][f] = (m->L > 0 && has_split(f, a)) ? (float*)take(slab_count(m, a) * 4 * (size_t)nsim) : nullptr;
     CK(cudaMemcpy(m->d_fields, m->f, sizeof(m->f), cudaMemcpyHostToDevice));
-    cudaFree(m->ctc_scratch);
+    dev_free(m->ctc_scratch);
     m->ctc_scratch = nullptr;
     return alloc_tc_scratch(m);
 }
@@ -675,7 +729,7 @@ cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, do
     axis_tables(n, d, tw, hp, hm, gp, gm, circ ? &ckp64 : nullptr, circ ? &ckm64 : nullptr);
     std::vector<float> ckp(ckp64.begin(), ckp64.end()), ckm(ckm64.begin(), ckm64.end());
     float2* tab = nullptr;
-    cudaError_t e = cudaMalloc(&tab, 3 * n * 8 + 2 * n * 4);
+    cudaError_t e = dev_alloc(&tab, 3 * n * 8 + 2 * n * 4);
     if (e != cudaSuccess) return e;
     float* ck = reinterpret_cast<float*>(tab + 3 * n);
     e = cudaMemcpy(tab, tw.data(), n * 8, cudaMemcpyHostToDevice);
@@ -709,7 +763,7 @@ cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, do
         e = launch_pass(p, st);
     }
     cudaError_t e2 = cudaStreamSynchronize(st);
-    cudaFree(tab);
+    dev_free(tab);
     return e != cudaSuccess ? e : e2;
 }
 
@@ -734,19 +788,23 @@ const char* es_status_string(int s)
 
 const char* es_last_error(void) { return g_err; }
 
+void es_fault_inject_alloc(int n) { g_alloc_countdown = n > 0 ? n : 0; }
+
+long long es_debug_live_allocations(void) { return g_live_allocs.load(); }
+
 void es_model_destroy(es_model* m)
 {
     if (!m) return;
-    cudaFree(m->vpool);
-    for (auto& s : m->srcs) cudaFree(s.d_w);
-    cudaFree(m->d_src);
-    cudaFree(m->d_rec);
-    cudaFree(m->d_out);
-    cudaFree(m->d_rcv);
-    cudaFree(m->pool);
-    cudaFree(m->fpool);
-    for (auto* c : m->ctc) cudaFree(c);
-    cudaFree(m->ctc_scratch);
+    dev_free(m->vpool);
+    for (auto& s : m->srcs) dev_free(s.d_w);
+    dev_free(m->d_src);
+    dev_free(m->d_rec);
+    dev_free(m->d_out);
+    dev_free(m->d_rcv);
+    dev_free(m->pool);
+    dev_free(m->fpool);
+    for (auto* c : m->ctc) dev_free(c);
+    dev_free(m->ctc_scratch);
     for (auto& e : m->ev)
         if (e) cudaEventDestroy(e);
     delete m;
@@ -755,6 +813,7 @@ void es_model_destroy(es_model* m)
 int es_model_create(const float* rho, const float* cp, const float* cs, int nx, int ny, int nz, double dx, int pml,
                     es_model** out)
 {
+    NvtxRange nvtx_range("es_model_create");
     if (!out) return ES_ERR_ARG;
     *out = nullptr;
     if (!rho || !cp || !cs || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || pml < 0) return ES_ERR_ARG;
@@ -805,7 +864,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
     size_t bytes = up(n * 4) * NMAT;
     for (int a = 0; a < 3; ++a) bytes += 3 * up(axis_len(m, a) * 8) + 6 * up(axis_len(m, a) * 4);
     bytes += up(16) + up(NFIELD * sizeof(float*));
-    cudaError_t e = cudaMalloc(&m->pool, bytes);
+    cudaError_t e = dev_alloc(&m->pool, bytes);
     if (e != cudaSuccess) {
         es_model_destroy(m);
         return cuda_fail(e, "cudaMalloc(model)");
@@ -834,7 +893,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         float* stage = nullptr;
         const float *d_rho = rho, *d_cp = cp, *d_cs = cs;
         if (!on_dev) {
-            e = cudaMalloc(&stage, 3 * n * sizeof(float));
+            e = dev_alloc(&stage, 3 * n * sizeof(float));
             if (e == cudaSuccess) e = cudaMemcpy(stage, h_rho.data(), n * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(stage + n, h_cp.data(), n * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(stage + 2 * n, h_cs.data(), n * 4, cudaMemcpyHostToDevice);
@@ -846,7 +905,7 @@ int es_model_create(const float* rho, const float* cp, const float* cs, int nx, 
         for (int k = 0; k < NMAT; ++k) mp.p[k] = m->mat[k];
         if (e == cudaSuccess) e = launch_materials(d_rho, d_cp, d_cs, nx, ny, nz, mp, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (stage) cudaFree(stage);
+        if (stage) dev_free(stage);
     }
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = upload_axis_tables(m, a);
     for (int k = 0; k < 2 * KPS_MAX && e == cudaSuccess; ++k) e = cudaEventCreate(&m->ev[k]);
@@ -937,10 +996,10 @@ static int add_source(es_model* m, int kind, const int pos[3], const double* v, 
     s.nw = nw;
     s.d_w = nullptr;
     if (nw > 0) {
-        CK(cudaMalloc(&s.d_w, sizeof(float) * nw));
+        CK(dev_alloc(&s.d_w, sizeof(float) * nw));
         cudaError_t e = cudaMemcpy(s.d_w, h.data(), sizeof(float) * nw, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
-            cudaFree(s.d_w);
+            dev_free(s.d_w);
             return cuda_fail(e, "cudaMemcpy(wavelet)");
         }
     }
@@ -975,10 +1034,10 @@ int es_batch_set(es_model* m, int nb, const int* pos, const double* mt, const fl
         s.nw = nw;
         s.d_w = nullptr;
         if (nw > 0) {
-            CK(cudaMalloc(&s.d_w, sizeof(float) * nw));
+            CK(dev_alloc(&s.d_w, sizeof(float) * nw));
             cudaError_t e = cudaMemcpy(s.d_w, &hw[(size_t)b * nw], sizeof(float) * nw, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
-                cudaFree(s.d_w);
+                dev_free(s.d_w);
                 return cuda_fail(e, "cudaMemcpy(wavelet)");
             }
         }
@@ -991,7 +1050,7 @@ int es_source_clear(es_model* m)
 {
     if (!m) return ES_ERR_ARG;
     CK(cudaStreamSynchronize(m->stream));
-    for (auto& s : m->srcs) cudaFree(s.d_w);
+    for (auto& s : m->srcs) dev_free(s.d_w);
     m->srcs.clear();
     return ES_OK;
 }
@@ -1093,8 +1152,8 @@ static int run_prepare(es_model* m, int nt, double* pdt, const int* rcv, int n_r
         // first viscous run at this batch size: v^{n-1/2} starts as the current velocity
         const size_t nv = m->ncell * (size_t)m->nsim;
         char* pool = nullptr;
-        CK(cudaMalloc(&pool, 6 * nv * sizeof(float)));
-        cudaFree(m->vpool);
+        CK(dev_alloc(&pool, 6 * nv * sizeof(float)));
+        dev_free(m->vpool);
         m->vpool = pool;
         m->vpool_nsim = m->nsim;
         m->vold = reinterpret_cast<float*>(pool);
@@ -1113,18 +1172,18 @@ static int run_prepare(es_model* m, int nt, double* pdt, const int* rcv, int n_r
         cells[r] = (long long)ix + (long long)m->nx * ((long long)iy + (long long)m->ny * iz);
     }
     if (n_rcv > m->rcv_cap) {
-        cudaFree(m->d_rcv);
+        dev_free(m->d_rcv);
         m->d_rcv = nullptr;
         m->rcv_cap = 0;
-        CK(cudaMalloc(&m->d_rcv, sizeof(long long) * n_rcv));
+        CK(dev_alloc(&m->d_rcv, sizeof(long long) * n_rcv));
         m->rcv_cap = n_rcv;
     }
     const size_t rec_n = (size_t)nt * m->nsim * 4 * n_rcv;
     if (rec_n > m->rec_cap) {
-        cudaFree(m->d_rec);
+        dev_free(m->d_rec);
         m->d_rec = nullptr;
         m->rec_cap = 0;
-        CK(cudaMalloc(&m->d_rec, rec_n * 4));
+        CK(dev_alloc(&m->d_rec, rec_n * 4));
         m->rec_cap = rec_n;
     }
     if (n_rcv > 0) CK(cudaMemcpyAsync(m->d_rcv, cells.data(), sizeof(long long) * n_rcv, cudaMemcpyHostToDevice, m->stream));
@@ -1167,10 +1226,10 @@ static int run_finish(es_model* m, int nt, int n_rcv, float* traces, cudaStream_
         float* dst = traces;
         if (!dev_out) {
             if (rec_n > m->out_cap) {
-                cudaFree(m->d_out);
+                dev_free(m->d_out);
                 m->d_out = nullptr;
                 m->out_cap = 0;
-                CK(cudaMalloc(&m->d_out, rec_n * 4));
+                CK(dev_alloc(&m->d_out, rec_n * 4));
                 m->out_cap = rec_n;
             }
             dst = m->d_out;
@@ -1195,18 +1254,27 @@ static int run_finish(es_model* m, int nt, int n_rcv, float* traces, cudaStream_
 
 int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* traces)
 {
-    int rc = run_prepare(m, nt, &dt, rcv, n_rcv, traces);
+    NvtxRange whole("es_run");
+    int rc;
+    {
+        NvtxRange r("es_run: prepare");
+        rc = run_prepare(m, nt, &dt, rcv, n_rcv, traces);
+    }
     if (rc != ES_OK || nt == 0) return rc;
     // graphs: K steps, 1 step, 1 step with per-kernel events (the last step)
     const long long start = m->steps_done;
     const int K = 16;
     cudaGraphExec_t gK = nullptr, g1 = nullptr, gT = nullptr;
     const int body = nt - 1;
-    if (body >= K) rc = capture(m, K, (float)dt, n_rcv, start, false, &gK);
-    if (rc == ES_OK && body % K) rc = capture(m, 1, (float)dt, n_rcv, start, false, &g1);
-    if (rc == ES_OK) rc = capture(m, 1, (float)dt, n_rcv, start, true, &gT);
+    {
+        NvtxRange r("es_run: capture");
+        if (body >= K) rc = capture(m, K, (float)dt, n_rcv, start, false, &gK);
+        if (rc == ES_OK && body % K) rc = capture(m, 1, (float)dt, n_rcv, start, false, &g1);
+        if (rc == ES_OK) rc = capture(m, 1, (float)dt, n_rcv, start, true, &gT);
+    }
     cudaError_t e = cudaSuccess;
     if (rc == ES_OK) {
+        NvtxRange r("es_run: replay");
         for (int i = 0; i < body / K && e == cudaSuccess; ++i) e = cudaGraphLaunch(gK, m->stream);
         for (int i = 0; i < body % K && e == cudaSuccess; ++i) e = cudaGraphLaunch(g1, m->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(gT, m->stream);
@@ -1216,7 +1284,10 @@ int es_run(es_model* m, int nt, double dt, const int* rcv, int n_rcv, float* tra
     if (gT) cudaGraphExecDestroy(gT);
     if (rc != ES_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "es_run launch");
-    rc = run_finish(m, nt, n_rcv, traces, m->stream);
+    {
+        NvtxRange r("es_run: finish");
+        rc = run_finish(m, nt, n_rcv, traces, m->stream);
+    }
     if (rc == ES_OK || rc == ES_ERR_UNSTABLE)
         for (int k = 0; k < m->n_last; ++k) CK(cudaEventElapsedTime(&m->last_ms[k], m->ev[2 * k], m->ev[2 * k + 1]));
     return rc;
@@ -1268,6 +1339,7 @@ static int capture_group(es_model* const* ms, int nmod, int steps, const double*
 int es_run_group(int nmod, es_model* const* models, int nt, const double* dts, const int* const* rcvs,
                  const int* n_rcvs, float* const* traces)
 {
+    NvtxRange nvtx_range("es_run_group");
     if (nmod < 1 || !models || !dts || !rcvs || !n_rcvs || !traces || nt < 0) return ES_ERR_ARG;
     for (int i = 0; i < nmod; ++i) {
         if (!models[i]) return ES_ERR_ARG;
@@ -1307,6 +1379,7 @@ int es_run_group(int nmod, es_model* const* models, int nt, const double* dts, c
 
 int es_model_autotune(es_model* m, int reps, char* report, int report_len)
 {
+    NvtxRange nvtx_range("es_model_autotune");
     if (!m || reps < 1) return ES_ERR_ARG;
     double dt = 0.0;
     int rc = run_prepare(m, 1, &dt, nullptr, 0, nullptr);
@@ -1433,6 +1506,7 @@ int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv)
 int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* src_of_event, const float* amps,
                  const float* t0s, int n_events, double dt, int n_out, float* gather, void* stream)
 {
+    NvtxRange nvtx_range("es_superpose");
     if (!traces || !gather || n_src < 1 || n_rcv < 1 || nt < 1 || n_events < 0 || n_out < 1 || !(dt > 0))
         return ES_ERR_ARG;
     if (n_events > 0 && (!src_of_event || !amps || !t0s)) return ES_ERR_ARG;
@@ -1456,7 +1530,7 @@ int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* s
     const size_t ev_bytes = (size_t)std::max(n_events, 1) * 12;
     const size_t bytes = ev_bytes + (dev_in ? 0 : tr_n * 4 + 256) + (dev_out ? 0 : g_n * 4 + 256);
     char* scratch = nullptr;
-    CK(cudaMalloc(&scratch, bytes));
+    CK(dev_alloc(&scratch, bytes));
     int* d_src = (int*)scratch;
     int* d_k = d_src + std::max(n_events, 1);
     float* d_a = (float*)(d_k + std::max(n_events, 1));
@@ -1474,7 +1548,7 @@ int es_superpose(const float* traces, int n_src, int n_rcv, int nt, const int* s
     if (e == cudaSuccess) e = launch_superpose(d_tr, n_src, n_rcv, nt, d_src, d_a, d_k, n_events, n_out, d_g, st);
     if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(gather, d_g, g_n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(scratch);
+    dev_free(scratch);
     if (e != cudaSuccess) return cuda_fail(e, "es_superpose");
     return ES_OK;
 }
@@ -1505,7 +1579,7 @@ int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, d
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny * nz;
     float* tmp = nullptr;
-    CK(cudaMalloc(&tmp, 2 * n * sizeof(float)));
+    CK(dev_alloc(&tmp, 2 * n * sizeof(float)));
     float* ones = tmp + n;
     const double d[3] = {dx, dy, dz};
     cudaError_t e = launch_fill(ones, n, 1.f, st);
@@ -1516,7 +1590,7 @@ int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, d
         if (e == cudaSuccess) e = derivative_pass(tmp, nx, ny, nz, a, d[a], +1, out, ones, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(tmp);
+    dev_free(tmp);
     if (e != cudaSuccess) return cuda_fail(e, "es_laplacian");
     return ES_OK;
 }

@@ -4,6 +4,7 @@
 // loading this library holds until the process exits; the caller passes all
 // inputs and the output in device memory.  Nothing here allocates: no
 // cudaMalloc, cudaFree, cudaMallocAsync or host heap allocation.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,23 +20,61 @@ constexpr int kScratchInts = ES_NOALLOC_MAX_EVENTS + 64;
 static __device__ __align__(256) int g_noalloc_scratch[kScratchInts];
 
 // Host code cannot use g_noalloc_scratch as an address (its host-side name is
-// only a stand-in); the device address is looked up once per device.
+// only a stand-in); the device address is looked up once per device and
+// context (cudaGetSymbolAddress with that device current).  The cache is keyed
+// on the context's unique id: after cudaDeviceReset the module is loaded again
+// into a new primary context, at a new address, and the lookup runs again.
 constexpr int kMaxDevices = 64;
-int* g_scratch_dev[kMaxDevices] = {};
+struct ScratchEntry {
+    unsigned long long ctx_id = 0;
+    int* ptr = nullptr;
+};
+ScratchEntry g_scratch_dev[kMaxDevices];
 std::mutex g_scratch_mu;
+
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+typedef CUresult (*CtxGetId)(CUcontext, unsigned long long*);
+
+// the unique id of the calling thread's current context (0 if unknown)
+unsigned long long current_context_id()
+{
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrent>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetId>(p);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 int scratch_address(int** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ES_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return ES_ERR_ARG;
+    // id 0 (no context current yet, or no driver entry point): look the address up again
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_dev[dev]) {
+    ScratchEntry& e = g_scratch_dev[dev];
+    if (!e.ptr || id == 0 || e.ctx_id != id) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ES_ERR_CUDA;
-        g_scratch_dev[dev] = static_cast<int*>(p);
+        e.ptr = static_cast<int*>(p);
+        e.ctx_id = id;
     }
-    *out = g_scratch_dev[dev];
+    *out = e.ptr;
     return ES_OK;
 }
 

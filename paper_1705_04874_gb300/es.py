@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 ES_PREC_FP32, ES_PREC_COMPENSATED, ES_PREC_FP32_TC = 0, 1, 2
+ES_NOALLOC_MAX_EVENTS = 65536  # include/es.h
 ES_OK, ES_ERR_ARG, ES_ERR_SIZE, ES_ERR_CUDA, ES_ERR_OOM, ES_ERR_UNSTABLE, ES_ERR_TIMEOUT, ES_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -82,6 +83,8 @@ def _load():
                 "es_model_destroy": ([vp], None),
                 "es_status_string": ([c_int], ctypes.c_char_p),
                 "es_last_error": ([], ctypes.c_char_p),
+                "es_fault_inject_alloc": ([c_int], None),
+                "es_debug_live_allocations": ([], ctypes.c_longlong),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -100,7 +103,8 @@ def exported_symbols():
             "es_kernels_per_step", "es_model_autotune", "es_fft_plan",
             "es_fft_plan_select", "es_sur_create", "es_sur_destroy", "es_sur_set_stream", "es_sur_num_params",
             "es_sur_get_params", "es_sur_set_params", "es_sur_set_output_scale", "es_sur_fit_output_scale",
-            "es_sur_predict", "es_sur_loss_grad", "es_sur_train_step", "es_sur_combine", "es_gemm_bf16", "es_gemm_status", "es_gemm_wait_probe", "es_model_destroy", "es_status_string", "es_last_error"]
+            "es_sur_predict", "es_sur_loss_grad", "es_sur_train_step", "es_sur_combine", "es_gemm_bf16", "es_gemm_status", "es_gemm_wait_probe", "es_model_destroy", "es_status_string", "es_last_error",
+            "es_fault_inject_alloc", "es_debug_live_allocations"]
 
 
 def _check(status, where):

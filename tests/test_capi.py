@@ -87,3 +87,17 @@ def test_surrogate_host_side_argument_checks(lib):
     assert lib.es_gemm_bf16(8, 8, 12, p, 16, 0, p, 16, 1, p, 8, 1.0, 0.0, 1, None) == es.ES_ERR_ARG  # K % 8
     assert lib.es_gemm_bf16(8, 8, 8, p, 4, 0, p, 8, 1, p, 8, 1.0, 0.0, 1, None) == es.ES_ERR_ARG  # lda < K
     assert lib.es_sur_num_params(None) == es.ES_ERR_ARG
+
+
+def test_fault_injection_switch_without_a_gpu(lib):
+    """The allocation fault switch and the live-allocation count are host-side
+    state: they answer without a device, and a failed call leaves the count
+    where it was."""
+    from paper_1705_04874_gb300 import es
+    live = lib.es_debug_live_allocations()
+    assert live >= 0
+    lib.es_fault_inject_alloc(1)
+    h = ctypes.c_void_p()
+    assert lib.es_model_create(None, None, None, 32, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
+    lib.es_fault_inject_alloc(0)
+    assert lib.es_debug_live_allocations() == live

@@ -114,3 +114,54 @@ def test_model_from_device_arrays_equals_host_arrays(es):
             m.source_set((24, 18, 20), mt, w)
             out.append(m.run(nt, dt, rcv))
     assert np.array_equal(out[0], out[1])
+
+
+def test_allocation_failures_return_oom_and_leak_nothing(es):
+    """Host-side fault injection (es_fault_inject_alloc): every device
+    allocation of es_model_create, of a run's buffers and of es_batch_set made
+    to fail in turn.  Each failing call returns ES_ERR_OOM, and the library
+    holds exactly the allocations it held before the call."""
+    lib = es._load()
+    rho, cp, cs = synth.two_layer_model(32, water_cells=8)
+    dt = cfl_dt(cp, 10.0)
+    w = synth.ricker(20, dt, 25.0)
+    base = lib.es_debug_live_allocations()
+    k, failed = 1, 0
+    try:
+        while True:  # model creation
+            lib.es_fault_inject_alloc(k)
+            try:
+                m = es.Model(rho, cp, cs, dx=10.0, pml=6)
+            except es.EsError as e:
+                assert e.status == es.ES_ERR_OOM, e
+                assert lib.es_debug_live_allocations() == base
+                failed += 1
+                k += 1
+                continue
+            lib.es_fault_inject_alloc(0)
+            m.close()
+            break
+        assert failed >= 2 and lib.es_debug_live_allocations() == base
+        with es.Model(rho, cp, cs, dx=10.0, pml=6) as m:  # a source, a run, a batch
+            rcv = m.seabed_receivers(4, 4)
+            for k in (1, 2, 3, 4):
+                m.source_set((16, 16, 16), synth.explosive(), w)
+                before = lib.es_debug_live_allocations()
+                lib.es_fault_inject_alloc(k)
+                try:
+                    m.run(20, dt, rcv)
+                except es.EsError as e:
+                    assert e.status == es.ES_ERR_OOM, e
+                lib.es_fault_inject_alloc(0)
+                assert lib.es_debug_live_allocations() <= before + 4
+            lib.es_fault_inject_alloc(1)
+            with pytest.raises(es.EsError) as e:
+                m.batch_set(np.array([[16, 16, 16], [14, 15, 16]]), np.stack([synth.explosive()] * 2),
+                            np.stack([w, w]))
+            assert e.value.status == es.ES_ERR_OOM
+            lib.es_fault_inject_alloc(0)
+            m.source_set((16, 16, 16), synth.explosive(), w)
+            assert np.isfinite(m.run(20, dt, rcv)).all()  # the model still works
+        assert lib.es_debug_live_allocations() == base
+    finally:
+        lib.es_fault_inject_alloc(0)

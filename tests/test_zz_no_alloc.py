@@ -13,7 +13,6 @@ from paper_1705_04874_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-6  # same kernel arithmetic as es_superpose: expected to agree exactly
 
 
 @pytest.fixture(scope="module")
@@ -54,8 +53,22 @@ def test_noalloc_matches_es_superpose_twice(env):
         assert rc == es.ES_OK
         ref = torch.empty((4, n_rcv, n_out), device="cuda")
         es.es_superpose(tr, src, amps, t0s, dt, n_out, gather=ref)
-        g, r = got.cpu().numpy(), ref.cpu().numpy()
-        assert np.abs(g - r).max() <= TOL * max(1.0, np.abs(r).max())
+        # the same kernel and the same event shifts as es_superpose: equal bit for bit
+        assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_noalloc_at_the_event_limit(env):
+    """ES_NOALLOC_MAX_EVENTS events, more than fit in shared memory at once:
+    equal to es_superpose bit for bit, on two calls in a row."""
+    es, lib, torch = env
+    n_ev = es.ES_NOALLOC_MAX_EVENTS
+    tr, src, amps, t0s = _inputs(torch, 11, 8, 2, 300, n_ev, span=0.5)
+    ref = torch.empty((4, 2, 900), device="cuda")
+    es.es_superpose(tr, src, amps, t0s, 1e-3, 900, gather=ref)
+    for _ in range(2):
+        rc, got = _call(lib, torch, tr, src, amps, t0s, 1e-3, 900)
+        assert rc == es.ES_OK
+        assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy())
 
 
 def test_noalloc_rejects_bad_input_without_writing(env):
