@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--sur-latent", type=int, default=768)
     ap.add_argument("--sur-nfreq", type=int, default=9)
     ap.add_argument("--sur-lr", type=float, default=3e-3)
+    ap.add_argument("--sur-random", type=int, default=10000, help="surrogate workload: sources at random cells")
     ap.add_argument("--nt", type=int, default=0, help="override time steps per es_run (diagnostics)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -338,7 +339,10 @@ def main():
         # runs the full 682-location, 4092-run one)
         sur_out, _ = surrogate_pipeline(128, 400, args.sur_lr, args.sur_hidden, args.sur_latent, args.sur_nfreq,
                                         gemm=False)
-        line["surrogate"] = {"value": sur_out["pipeline_seismograms_per_s"], "unit": "4C seismogram sets/s",
+        line["surrogate"] = {"value": sur_out["random_positions"]["pipeline_seismograms_per_s"],
+                             "value_is": "sources at random cells of the reservoir box (network where the gate "
+                                         "trusts it, solver elsewhere)",
+                             "unit": "4C seismogram sets/s",
                              "gate": "relative L2 <= 5 % (held-out, 0.8 margin); served sources checked",
                              **sur_out}
     if rank == 0:
@@ -721,7 +725,7 @@ def measure_configs(args):
 
 
 def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, gemm=True, serve_batch=1024,
-                       train_batch=256):
+                       train_batch=256, n_rand=1000, n_held=128):
     """The surrogate workflow on the 96^3 marine model (PML 10, 8 x 8 seabed
     receivers, 1024 samples, Ricker 30 Hz): a catalog of n_loc Latin-hypercube
     locations in the reservoir box whose 6 unit-moment responses come from
@@ -803,6 +807,48 @@ def surrogate_pipeline(n_loc, epochs, lr, hidden, latent, nfreq, n_src=10000, ge
         d[b:e] = ((served[b:e] - ref) / sc).reshape(e - b, -1).norm(dim=1) / (ref / sc).reshape(e - b, -1).norm(dim=1)
         del ref
     out["pipeline_sources"] = n_pipe
+    # sources away from the catalog: n_held held-out cells (not catalog locations) with exact
+    # solver references, the network against the two baselines, the position gate; then
+    # n_rand sources at random cells of the box served with the solver as the fallback
+    rng = synth.SplitMix64(21)
+    cand = synth.random_positions(rng, box, 4 * n_held)
+    _, dcand = sur.nearest_locations(locations, cand)
+    held = cand[dcand[:, 0] > 0][:n_held]
+    hmt = np.array([synth.random_dc(rng) for _ in held])
+    truth = sur.solver_references(m, held, hmt, nt, dt, rcv, wav, per_batch=64)
+    _, hd = sur.nearest_locations(locations, held)
+    hd = hd[:, 0]
+    e_net = sur.scaled_rel_l2(sur.predict_at(s, box, held, hmt), truth, sc)
+    e_near = sur.scaled_rel_l2(sur.baseline_nearest(G, locations, held, hmt), truth, sc)
+    e_idw = sur.scaled_rel_l2(sur.baseline_idw(G, locations, held, hmt), truth, sc)
+    del truth
+    d_star = sur.calibrate_position_gate(hd, e_net)
+    near1 = hd <= 1.5
+    out["off_catalog"] = {
+        "held_out_sources": int(len(held)), "median_distance_cells": round(float(np.median(hd)), 2),
+        "network_median_rel_l2": round(float(np.median(e_net)), 4),
+        "nearest_location_median_rel_l2": round(float(np.median(e_near)), 4),
+        "idw8_median_rel_l2": round(float(np.median(e_idw)), 4),
+        "within_1.5_cells": {"n": int(near1.sum()),
+                             "network": round(float(np.median(e_net[near1])), 4) if near1.any() else None,
+                             "nearest": round(float(np.median(e_near[near1])), 4) if near1.any() else None},
+        "network_within_5pct": round(float((e_net < 0.05).mean()), 4),
+        "network_beats_nearest": round(float((e_net < e_near).mean()), 4),
+        "network_beats_idw8": round(float((e_net < e_idw).mean()), 4),
+        "position_gate_d_star": d_star}
+    rnd = synth.random_positions(synth.SplitMix64(31), box, n_rand)
+    rmt = np.array([synth.random_dc(rng) for _ in rnd])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    served_r, used_r = sur.serve_positions(s, box, trusted, d_star, locations, rnd, rmt, m, nt, dt, rcv, wav,
+                                           batch_solver=64)
+    torch.cuda.synchronize()
+    t_r = time.perf_counter() - t0
+    del served_r
+    out["random_positions"] = {"sources": int(n_rand), "pipeline_seismograms_per_s": round(n_rand / t_r, 2),
+                               "pipeline_solver_fraction": round(float(used_r.mean()), 4),
+                               "network_fraction": round(float(1 - used_r.mean()), 4),
+                               "speedup_vs_solver": round(n_rand / t_r / solver_rate, 3)}
     out.update({"solver_seismograms_per_s": round(solver_rate, 2), "surrogate_seismograms_per_s": round(sur_rate, 1),
                 "pipeline_seismograms_per_s": round(pipe_rate, 1),
                 "pipeline_solver_fraction": round(float(used_solver.mean()), 4),
@@ -858,11 +904,13 @@ def decoder_roofline(tflops, M, N, K):
 
 def measure_surrogate(args):
     """Surrogate workload (C5): 682 catalog locations x 6 unit moment tensors
-    (4092 solver runs), training, gate, 10,000 served sources.  Metric:
-    seismograms/s of the served pipeline."""
+    (4092 solver runs), training, the gates, 10,000 sources at catalog
+    locations and 10,000 at random cells of the reservoir box served (the
+    latter mostly by the solver fallback).  Metric: seismograms/s of the served
+    pipeline on the random cells."""
     out, roof = surrogate_pipeline(args.sur_locations, args.sur_epochs, args.sur_lr, args.sur_hidden,
-                                   args.sur_latent, args.sur_nfreq)
-    print(json.dumps({"metric": "seismograms/s", "value": out["pipeline_seismograms_per_s"],
+                                   args.sur_latent, args.sur_nfreq, n_rand=args.sur_random)
+    print(json.dumps({"metric": "seismograms/s", "value": out["random_positions"]["pipeline_seismograms_per_s"],
                       "unit": "4C seismogram sets/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16/f32",
                       "data": "synthetic", "config": {"workload": out["workload"]}, "roofline": roof,
                       "surrogate": out}))

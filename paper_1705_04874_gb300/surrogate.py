@@ -352,3 +352,130 @@ def serve(sur, pos_n, trusted, loc, mt, solver_model, locations, nt, dt, rcv, wa
         solver_model.run(nt, dt, rcv_d, tr)
         out[torch.from_numpy(part).cuda()] = tr
     return out, ~use_sur
+
+
+# ---------------------------------------------------------------------------
+# sources away from the catalog: exact references, baselines, the position
+# gate and serving with the solver as the fallback
+# ---------------------------------------------------------------------------
+
+def solver_references(model, pos, mt, nt, dt, rcv, wavelet, per_batch=32):
+    """Exact 4C seismograms [B][4][n_rcv][nt] (CUDA) of moment-tensor sources at
+    arbitrary grid cells, from batched solver runs (one simulation per source).
+    model: an es.Model (its sources and batch are replaced)."""
+    import torch
+    B, n_rcv = len(pos), len(rcv)
+    out = torch.empty((B, 4, n_rcv, nt), device="cuda")
+    rcv_d = torch.from_numpy(np.ascontiguousarray(rcv, np.int32)).cuda()
+    for s in range(0, B, per_batch):
+        part = np.arange(s, min(B, s + per_batch))
+        wav = np.tile(np.asarray(wavelet, np.float32), (len(part), 1))
+        model.batch_set(np.asarray(pos, np.int32)[part], np.asarray(mt)[part], wav)
+        model.run(nt, dt, rcv_d, out[s:s + len(part)])
+    return out
+
+
+def nearest_locations(locations, pos, k=1):
+    """The k catalog locations nearest to each position (Euclidean distance in
+    cells): (indices [B][k], distances [B][k])."""
+    loc = np.asarray(locations, np.float64)
+    p = np.asarray(pos, np.float64)
+    d2 = ((p[:, None, :] - loc[None, :, :]) ** 2).sum(axis=2)
+    idx = np.argsort(d2, axis=1, kind="stable")[:, :k]
+    return idx, np.sqrt(np.take_along_axis(d2, idx, axis=1))
+
+
+def baseline_nearest(G, locations, pos, mt):
+    """Baseline without a network: the exact seismogram of the same moment
+    tensor at the nearest catalog location."""
+    idx, _ = nearest_locations(locations, pos, 1)
+    return combine(G, idx[:, 0], mt)
+
+
+def baseline_idw(G, locations, pos, mt, k=8):
+    """Baseline without a network: the catalog interpolated to the position by
+    inverse-distance-squared weights over its k nearest locations (each term
+    the exact seismogram of the weighted moment tensor there; at a catalog
+    location, that location alone)."""
+    idx, dist = nearest_locations(locations, pos, k)
+    w = 1.0 / np.maximum(dist, 1e-9) ** 2
+    w = np.where(dist[:, :1] < 1e-9, (dist < 1e-9).astype(np.float64), w)
+    w /= w.sum(axis=1, keepdims=True)
+    mt = np.asarray(mt, np.float64)
+    out = None
+    for j in range(k):
+        part = combine(G, idx[:, j], w[:, j:j + 1] * mt)
+        out = part if out is None else out.add_(part)
+    return out
+
+
+def predict_at(sur, box, pos, mt):
+    """The network's seismograms [B][4][n_rcv][nt] for sources at arbitrary
+    cells of the box (positions normalised as for training)."""
+    import torch
+    B = len(pos)
+    pn = normalize_positions(pos, box)
+    out = torch.empty((B, sur.D), device="cuda")
+    for s in range(0, B, sur.max_batch):
+        n = min(sur.max_batch, B - s)
+        m = (n + 7) // 8 * 8
+        idx = np.concatenate([np.arange(s, s + n), np.full(m - n, s)])
+        y = sur.predict(torch.from_numpy(pn[idx]).cuda(), torch.from_numpy(np.asarray(mt, np.float32)[idx]).cuda())
+        out[s:s + n] = y[:n]
+    return out.view(B, 4, -1, sur.cfg.nt)
+
+
+def component_scale(G):
+    """RMS of each of the 4 components over the catalog, shape [1][4][1][1]:
+    the weights of the whole-seismogram relative L2 (pressure and velocity
+    differ by orders of magnitude)."""
+    return G.permute(2, 0, 1, 3, 4).reshape(4, -1).pow(2).mean(dim=1).sqrt().view(1, 4, 1, 1)
+
+
+def scaled_rel_l2(pred, truth, scale):
+    """Per source, the relative L2 of the 4C seismogram with each component
+    divided by its scale; numpy [B]."""
+    B = truth.shape[0]
+    d = ((pred - truth) / scale).reshape(B, -1).norm(dim=1)
+    return (d / (truth / scale).reshape(B, -1).norm(dim=1)).cpu().numpy()
+
+
+def calibrate_position_gate(dist, err, threshold=0.05, margin=0.8):
+    """Gate for sources away from the catalog from held-out sources: the
+    largest distance d* to the nearest catalog location such that every
+    held-out source at a distance up to d* (and above 0) has an error below
+    margin * threshold; -1 when the nearest off-catalog held-out source is
+    already above it (only catalog locations are served by the network)."""
+    dist, err = np.asarray(dist, np.float64), np.asarray(err, np.float64)
+    off = dist > 0
+    order = np.argsort(dist[off], kind="stable")
+    ds, es_ = dist[off][order], err[off][order]
+    ok = es_ <= margin * threshold
+    if len(ds) == 0 or not ok[0]:
+        return -1.0
+    first_bad = np.argmin(ok) if not ok.all() else len(ok)
+    return float(ds[first_bad - 1])
+
+
+def serve_positions(sur, box, trusted_loc, d_star, locations, pos, mt, solver_model, nt, dt, rcv, wavelet,
+                    batch_solver=32, out=None):
+    """Seismograms for sources at arbitrary cells: the network where the source
+    sits on a catalog location the location gate trusts, or within d_star cells
+    of the catalog; the solver (batched runs at the exact positions) elsewhere.
+    Returns (traces CUDA [B][4][n_rcv][nt], used_solver bool [B])."""
+    import torch
+    B, n_rcv = len(pos), len(rcv)
+    if out is None:
+        out = torch.empty((B, 4, n_rcv, nt), device="cuda")
+    idx, dist = nearest_locations(locations, pos, 1)
+    on_cat = dist[:, 0] < 1e-9
+    use_sur = np.where(on_cat, np.asarray(trusted_loc)[idx[:, 0]], dist[:, 0] <= d_star)
+    net = np.nonzero(use_sur)[0]
+    if len(net):
+        out[torch.from_numpy(net).cuda()] = predict_at(sur, box, np.asarray(pos)[net], np.asarray(mt)[net])
+    rest = np.nonzero(~use_sur)[0]
+    if len(rest):
+        ref = solver_references(solver_model, np.asarray(pos)[rest], np.asarray(mt)[rest], nt, dt, rcv, wavelet,
+                                per_batch=batch_solver)
+        out[torch.from_numpy(rest).cuda()] = ref
+    return out, ~use_sur

@@ -270,3 +270,56 @@ def test_catalog_train_gate_serve(env):
             assert used_solver.sum() == (~trusted[loc]).sum()
         finally:
             s.close()
+
+
+def test_sources_away_from_the_catalog(env):
+    """Sources at cells that are not catalog locations: their exact references
+    come from fresh solver runs; the network is compared with the two baselines
+    without one (the nearest catalog location, inverse-distance interpolation
+    of the catalog); the position gate, calibrated on held-out cells, decides
+    which of them the network may serve.  Every served seismogram -- network
+    or solver fallback -- is within 5 % of its exact reference, and the
+    fallback runs for the off-catalog sources the gate refuses."""
+    es, sur, torch = env
+    shape = (48, 32, 32)
+    rho, cp, cs = synth.marine_model(shape=shape, seed=4)
+    pml, nt = 4, 256
+    dt = cfl_dt(cp, 10.0)
+    wav = synth.ricker(nt, dt, 30.0)
+    box = synth.reservoir_box(shape, pml)
+    rng = synth.SplitMix64(6)
+    locations = synth.latin_hypercube_positions(rng, box, 24)
+    with es.Model(rho, cp, cs, dx=10.0, pml=pml) as m:
+        rcv = m.seabed_receivers(2, 2)
+        G = sur.green_catalog(m, locations, nt, dt, rcv, wav, per_batch=8)
+        sc = sur.component_scale(G)
+        s = sur.Surrogate(len(rcv), nt, nfreq=3, hidden=128, latent=64, max_batch=48, seed=1)
+        try:
+            sur.train(s, sur.normalize_positions(locations, box), G, epochs=200, lr=3e-3)
+            trusted, _ = sur.calibrate_gate(s, sur.normalize_positions(locations, box), G, n_val=3)
+            # held-out cells off the catalog
+            cand = synth.random_positions(synth.SplitMix64(12), box, 64)
+            _, dc = sur.nearest_locations(locations, cand)
+            held = cand[dc[:, 0] > 0][:16]
+            hmt = np.array([synth.random_dc(rng) for _ in held])
+            truth = sur.solver_references(m, held, hmt, nt, dt, rcv, wav)
+            _, hd = sur.nearest_locations(locations, held)
+            e_net = sur.scaled_rel_l2(sur.predict_at(s, box, held, hmt), truth, sc)
+            e_near = sur.scaled_rel_l2(sur.baseline_nearest(G, locations, held, hmt), truth, sc)
+            e_idw = sur.scaled_rel_l2(sur.baseline_idw(G, locations, held, hmt), truth, sc)
+            assert np.isfinite(e_net).all() and np.isfinite(e_near).all() and np.isfinite(e_idw).all()
+            print(f"off-catalog: within 5 % {np.mean(e_net < 0.05):.3f}; median error network {np.median(e_net):.3f}, "
+                  f"nearest location {np.median(e_near):.3f}, inverse-distance {np.median(e_idw):.3f}")
+            d_star = sur.calibrate_position_gate(hd[:, 0], e_net)
+            # a mix of catalog and off-catalog sources, not the held-out ones
+            pos = np.concatenate([locations[:8], cand[dc[:, 0] > 0][16:24]])
+            mts = np.array([synth.random_dc(rng) for _ in pos])
+            out, used = sur.serve_positions(s, box, trusted, d_star, locations, pos, mts, m, nt, dt, rcv, wav)
+            ref = sur.solver_references(m, pos, mts, nt, dt, rcv, wav)
+            err = sur.scaled_rel_l2(out, ref, sc)
+            assert err.max() < 0.05, err
+            _, pd = sur.nearest_locations(locations, pos)
+            assert used[pd[:, 0] > max(d_star, 0)].all()  # beyond the gate's distance: the solver
+            assert used.any() and (~used[:8]).sum() == trusted[:8].sum()
+        finally:
+            s.close()
