@@ -36,11 +36,11 @@ __global__ void inject_kernel(float* const* fields, long long fstride, const Sou
             if (kind == 0) {
                 // moment tensor: stress component i gains M_i w[n] (Mxx Myy Mzz Mxy Mxz Myz)
                 for (int c = 0; c < 6; ++c)
-                    if (s.m[c] != 0.f) fields[SXX + c][q] += s.m[c] * w;
+                    if (s.m[c] != 0.f) fields[SXX + c][q] = __fmaf_rn(s.m[c], w, fields[SXX + c][q]);
             } else {
                 // point force: m[c] = dt f_c / (rho_c dx dy dz), folded on the host
                 for (int c = 0; c < 3; ++c)
-                    if (s.m[c] != 0.f) fields[VX + c][q] += s.m[c] * w;
+                    if (s.m[c] != 0.f) fields[VX + c][q] = __fmaf_rn(s.m[c], w, fields[VX + c][q]);
             }
         }
     }
@@ -171,8 +171,8 @@ __global__ void record_kernel(float* const* fields, long long fstride, int nsim,
     const int r = i % n_rcv, sim = i / n_rcv;
     const long long q = (long long)sim * fstride + rcv_cell[r];
     const size_t row = ((size_t)(*cur - start) * nsim + sim) * 4 * n_rcv;
-    const float s = fields[SXX][q] + fields[SYY][q] + fields[SZZ][q];
-    rec[row + r] = -s / 3.f;  // Eq. (3)
+    const float s = __fadd_rn(__fadd_rn(fields[SXX][q], fields[SYY][q]), fields[SZZ][q]);
+    rec[row + r] = __fdiv_rn(-s, 3.f);  // Eq. (3)
     rec[row + n_rcv + r] = fields[VX][q];
     rec[row + 2 * (size_t)n_rcv + r] = fields[VY][q];
     rec[row + 3 * (size_t)n_rcv + r] = fields[VZ][q];

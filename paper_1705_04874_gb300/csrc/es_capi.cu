@@ -351,6 +351,13 @@ struct es_model {
     long long* d_rcv = nullptr;
     int rcv_cap = 0;
     long long steps_done = 0;
+    // fused point sources and receivers (FFT passes only): per-CTA cell lists of the velocity z,
+    // stress y and stress z passes, one device buffer (build_special)
+    bool fused = false;
+    char* d_sp = nullptr;
+    size_t sp_cap = 0;
+    const int* sp_off[3] = {};
+    const SpecialCell* sp_cells[3] = {};
     cudaEvent_t ev[2 * KPS_MAX] = {};
     float last_ms[KPS_MAX] = {};
     int n_last = 0;
@@ -419,6 +426,10 @@ int upload_sources(es_model* m, double dt)
     return ES_OK;
 }
 
+// whether the point sources and receivers of a run go into the passes (every axis an FFT pass,
+// no smoothed source) or through the separate injection and recording kernels
+bool fused_sources(const es_model* m);
+
 // twiddles, spectral multipliers and (for a circulant axis) the kernels of axis a
 // whether axis a of the model runs through the circulant passes
 bool circ_axis(const es_model* m, int a) { return m->prec == ES_PREC_COMPENSATED || !fft_axis(axis_len(m, a), m->nx); }
@@ -482,6 +493,78 @@ cudaError_t upload_axis_tables(es_model* m, int a)
         }
     }
     return e;
+}
+
+bool fused_sources(const es_model* m)
+{
+    for (int a = 0; a < 3; ++a)
+        if (circ_axis(m, a)) return false;
+    return std::none_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.smooth != 0; });
+}
+
+// The per-CTA cell lists of the fused passes (PassParams::sp_off / sp): for the velocity z pass
+// (SP_VEL_Z) the point forces, then the receivers; for the stress y pass (SP_STR_Y) the moment
+// sources; for the stress z pass (SP_STR_Z) the moment sources, then the receivers.  A y or z pass
+// CTA owns 32 consecutive x at one z (y pass) or one y (z pass) of one simulation: blockIdx.x =
+// sim + nsim (x / 32 + ntx outer).  Sources keep their order (the order the injection kernel adds
+// them in).
+int build_special(es_model* m, const std::vector<long long>& rcv_cells)
+{
+    const int ntx = (m->nx + 31) / 32;
+    const int axis_of[3] = {2, 1, 2};
+    std::vector<SpecialCell> cells[3];
+    std::vector<int> off[3];
+    for (int k = 0; k < 3; ++k) {
+        const int mode = k + 1, axis = axis_of[k];
+        const size_t nb = (size_t)ntx * (axis == 1 ? m->nz : m->ny) * m->nsim;
+        auto block_of = [&](long long cell, int sim) {
+            const long long x = cell % m->nx, y = (cell / m->nx) % m->ny, z = cell / ((long long)m->nx * m->ny);
+            const long long tile = x / 32 + (long long)ntx * (axis == 1 ? z : y);
+            return (size_t)sim + (size_t)m->nsim * (size_t)tile;
+        };
+        std::vector<std::vector<SpecialCell>> per(nb);
+        for (size_t e = 0; e < m->srcs.size(); ++e) {
+            const Src& s = m->srcs[e];
+            if (s.smooth || (mode == SP_VEL_Z ? s.kind != 1 : s.kind != 0)) continue;
+            const long long cell = (long long)s.pos[0] + (long long)m->nx * ((long long)s.pos[1] + (long long)m->ny * s.pos[2]);
+            per[block_of(cell, s.sim)].push_back(
+                {(long long)s.sim * (long long)m->ncell + cell, s.kind == 1 ? SP_FORCE : SP_MOMENT, (int)e, s.sim});
+        }
+        if (mode != SP_STR_Y)
+            for (int sim = 0; sim < m->nsim; ++sim)
+                for (size_t r = 0; r < rcv_cells.size(); ++r)
+                    per[block_of(rcv_cells[r], sim)].push_back(
+                        {(long long)sim * (long long)m->ncell + rcv_cells[r], SP_RECEIVER, (int)r, sim});
+        off[k].assign(nb + 1, 0);
+        for (size_t b = 0; b < nb; ++b) {
+            off[k][b + 1] = off[k][b] + (int)per[b].size();
+            cells[k].insert(cells[k].end(), per[b].begin(), per[b].end());
+        }
+    }
+    const size_t A = 256;
+    auto up = [&](size_t b) { return (b + A - 1) / A * A; };
+    size_t bytes = 0;
+    for (int k = 0; k < 3; ++k) bytes += up(std::max<size_t>(1, cells[k].size()) * sizeof(SpecialCell)) + up(off[k].size() * 4);
+    if (bytes > m->sp_cap) {
+        dev_free(m->d_sp);
+        m->d_sp = nullptr;
+        m->sp_cap = 0;
+        CK(dev_alloc(&m->d_sp, bytes));
+        m->sp_cap = bytes;
+    }
+    char* cur = m->d_sp;
+    for (int k = 0; k < 3; ++k) {
+        m->sp_cells[k] = reinterpret_cast<const SpecialCell*>(cur);
+        if (!cells[k].empty())
+            CK(cudaMemcpyAsync(cur, cells[k].data(), cells[k].size() * sizeof(SpecialCell), cudaMemcpyHostToDevice,
+                               m->stream));
+        cur += up(std::max<size_t>(1, cells[k].size()) * sizeof(SpecialCell));
+        m->sp_off[k] = reinterpret_cast<const int*>(cur);
+        CK(cudaMemcpyAsync(cur, off[k].data(), off[k].size() * 4, cudaMemcpyHostToDevice, m->stream));
+        cur += up(off[k].size() * 4);
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    return ES_OK;
 }
 
 PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
@@ -572,16 +655,31 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
     const bool has_force = std::any_of(m->srcs.begin(), m->srcs.end(), [](const Src& s) { return s.kind == 1; });
     static const char* kVel[3] = {"vel-x", "vel-y", "vel-z"};
     static const char* kStr[3] = {"str-x", "str-y", "str-z"};
+    const bool fused = m->fused;
+    // the fused passes' source / receiver work (PassParams::sp_mode)
+    auto fuse = [&](PassParams& p, int mode) {
+        if (!fused) return;
+        p.step_now = m->d_int;
+        p.sp_mode = mode;
+        p.sp_off = m->sp_off[mode - 1];
+        p.sp = m->sp_cells[mode - 1];
+        p.src = m->d_src;
+        p.rec = m->d_rec;
+        p.rec_start = start;
+        p.n_rcv = n_rcv;
+    };
     for (int a = 0; a < 3; ++a) {
         NvtxRange r(kVel[a]);
         PassParams p = make_pass(m, a, false, dt);
         p.pdl = a == 0 ? 2 : 1;  // the x pass reads what the stress half wrote; y and z only add after it
+        if (fused && a == 0) p.step_counter = m->d_int;  // step index = counter - 1 from here on
+        if (a == 2) fuse(p, SP_VEL_Z);                     // point forces, then the velocity samples
         mark(true);
         CK(launch_pass(p, st));
         mark(false);
         ++k;
     }
-    if (has_force) {
+    if (has_force && !fused) {
         mark(true);
         CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 1, m->nx, m->ny, m->d_int,
                          m->d_int + 1, 0, st));
@@ -609,10 +707,16 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
                 for (int c = 0; c < 3; ++c)
                     if (p.job[j].src == m->f[VX + c]) p.job[j].src = m->wv + (size_t)c * nv;
         }
+        if (a == 1) fuse(p, SP_STR_Y);  // Mxy: sxy's last update is the y pass
+        if (a == 2) fuse(p, SP_STR_Z);  // the other moment components, then the pressure samples
         mark(true);
         CK(launch_pass(p, st));
         mark(false);
         ++k;
+    }
+    if (fused) {
+        *nk = k;
+        return ES_OK;
     }
     mark(true);
     CK(launch_inject(m->d_fields, (long long)m->ncell, m->d_src, (int)m->srcs.size(), 0, m->nx, m->ny, m->d_int,
@@ -805,6 +909,7 @@ void es_model_destroy(es_model* m)
     dev_free(m->fpool);
     for (auto* c : m->ctc) dev_free(c);
     dev_free(m->ctc_scratch);
+    dev_free(m->d_sp);
     for (auto& e : m->ev)
         if (e) cudaEventDestroy(e);
     delete m;
@@ -1210,6 +1315,8 @@ static int run_prepare(es_model* m, int nt, double* pdt, const int* rcv, int n_r
         CK(cudaStreamSynchronize(m->stream));
     }
     if ((rc = upload_sources(m, dt)) != ES_OK) return rc;
+    m->fused = fused_sources(m);
+    if (m->fused && (rc = build_special(m, cells)) != ES_OK) return rc;
     return ES_OK;
 }
 
@@ -1478,6 +1585,8 @@ int es_kernels_per_step(const es_model* m)
     // an axis on the tensor cores adds a field-update kernel to each of its two passes
     int tc = 0;
     for (int a = 0; a < 3; ++a) tc += tc_axis(m, a) ? 2 : 0;
+    // fused point sources and receivers: the six passes alone
+    if (fused_sources(m)) return 6 + (m->tau > 0.0 ? 1 : 0);
     return 8 + (has_force ? 1 : 0) + (m->tau > 0.0 ? 1 : 0) + tc;
 }
 

@@ -46,6 +46,28 @@ struct PassJob {
     float g[NEAR_TAPS];   // FFT passes: near taps of D(sign) (the multiplier tables hold H_far / n)
 };
 
+struct SourceDev {
+    int kind;            // 0 moment, 1 force
+    int smooth;          // 1: spread over the 5 x 5 x 5 Blackman stencil (moment sources)
+    int sim;             // simulation the source belongs to
+    long long cell;      // linear index
+    float m[6];          // moment (Mxx Myy Mzz Mxy Mxz Myz) or force scale per component
+    const float* w;      // wavelet samples (device)
+    int nw;
+};
+
+// A cell where a fused pass injects a point source or records a receiver after
+// its own field updates: q = linear index including the simulation's offset.
+enum { SP_MOMENT = 0, SP_FORCE = 1, SP_RECEIVER = 2 };
+struct SpecialCell {
+    long long q;
+    int kind;   // SP_MOMENT / SP_FORCE: idx = source; SP_RECEIVER: idx = receiver
+    int idx;
+    int sim;
+};
+// Which fused work a pass does in its special phase.
+enum { SP_NONE = 0, SP_VEL_Z = 1, SP_STR_Y = 2, SP_STR_Z = 3 };
+
 struct PassParams {
     int nx, ny, nz;
     int axis;             // 0 = x, 1 = y, 2 = z
@@ -73,6 +95,21 @@ struct PassParams {
     const __nv_bfloat16* ctc;  // long circulant axes: the kernel matrices split in three BF16 parts,
                                // [D+, D-][split][outputs][inputs], each pad64(n) x pad64(n) (circ_tc.cu)
     float* scratch;            // that pass's derivatives, [job][sim][cell], before the field update
+    // Point sources and receivers fused into the passes (FFT passes only): the first pass of a
+    // step advances the device step counter (step_counter); the velocity z pass injects the
+    // point forces and records the velocities, the stress y pass injects Mxy, the stress z pass
+    // the other moment components and records the pressure.  sp_off[b] .. sp_off[b + 1] are
+    // CTA b's (blockIdx.x) cells in sp, in source order, then receivers.  The step index is
+    // *step_now - 1; samples go to rec[(n - rec_start) nsim + sim][4][n_rcv].
+    int* step_counter;
+    const int* step_now;
+    int sp_mode;
+    const int* sp_off;
+    const SpecialCell* sp;
+    const SourceDev* src;
+    float* rec;
+    long long rec_start;
+    int n_rcv;
 };
 
 // Plan of the two-stage FFT for an axis length (0 if unsupported).
@@ -104,16 +141,6 @@ cudaError_t prepare_circ_kernels();
 cudaError_t prepare_pass_kernels();
 
 // ---- auxiliary kernels (aux_kernels.cu) ----
-struct SourceDev {
-    int kind;            // 0 moment, 1 force
-    int smooth;          // 1: spread over the 5 x 5 x 5 Blackman stencil (moment sources)
-    int sim;             // simulation the source belongs to
-    long long cell;      // linear index
-    float m[6];          // moment (Mxx Myy Mzz Mxy Mxz Myz) or force scale per component
-    const float* w;      // wavelet samples (device)
-    int nw;
-};
-
 cudaError_t launch_inject(float* const* fields, long long fstride, const SourceDev* src, int nsrc, int kind,
                           int nx, int ny, int* counter, int* cur, int advance, cudaStream_t st);
 // rec[n - start][sim][4][n_rcv]

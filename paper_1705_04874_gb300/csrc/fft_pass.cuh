@@ -487,6 +487,65 @@ inline cudaError_t launch_pass_kernel(K kernel, dim3 grid, int threads, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, p);
 }
 
+// Fused point sources and receivers of this CTA (PassParams::sp_mode): once
+// the CTA's own field updates are done (a CTA barrier makes its threads'
+// reductions visible to the CTA; the reads go through L2), thread 0 adds the
+// sources in their order, and after a second barrier every receiver is
+// recorded by a thread of its own -- the arithmetic of the separate injection
+// and recording kernels (inject_kernel, record_kernel).  job = the CTA's job
+// (blockIdx.y): the velocity z pass's job c updates v_c, the stress y pass's
+// job 1 sxy, the stress z pass's job 0 sxx syy szz, job 1 sxz, job 2 syz.
+__device__ __forceinline__ void special_phase(const PassParams& p, const PassJob& J, int job)
+{
+    const int b0 = p.sp_off[blockIdx.x], b1 = p.sp_off[blockIdx.x + 1];
+    if (b0 == b1) return;  // the same for every thread of the CTA
+    const int n = *p.step_now - 1;
+    __syncthreads();
+    if (p.sp[b0].kind != SP_RECEIVER) {  // sources come first in the list
+        if (threadIdx.x == 0) {
+            if (p.pdl == 1) pdl_wait();  // (done already if this thread had cells to update)
+            for (int e = b0; e < b1; ++e) {
+                const SpecialCell c = p.sp[e];
+                if (c.kind == SP_RECEIVER) break;
+                const SourceDev& s = p.src[c.idx];
+                if (n >= s.nw) continue;
+                const float w = s.w[n];
+                auto add = [&](float* t, float m) {
+                    if (m != 0.f) *t = __fmaf_rn(m, w, __ldcg(t));
+                };
+                if (p.sp_mode == SP_VEL_Z) {
+                    if (c.kind == SP_FORCE) add(J.tgt[0] + c.q, s.m[job]);
+                } else if (c.kind == SP_MOMENT) {
+                    if (p.sp_mode == SP_STR_Y) {
+                        if (job == 1) add(J.tgt[0] + c.q, s.m[3]);
+                    } else if (job == 0) {
+                        add(J.tgt[0] + c.q, s.m[0]);
+                        add(J.tgt[1] + c.q, s.m[1]);
+                        add(J.tgt[2] + c.q, s.m[2]);
+                    } else {
+                        add(J.tgt[0] + c.q, s.m[job == 1 ? 4 : 5]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (p.sp_mode == SP_STR_Y || (p.sp_mode == SP_STR_Z && job != 0)) return;
+    if (p.pdl == 1) pdl_wait();
+    for (int e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+        const SpecialCell c = p.sp[e];
+        if (c.kind != SP_RECEIVER) continue;
+        float* row = p.rec + ((size_t)(n - p.rec_start) * p.nsim + c.sim) * 4 * p.n_rcv;
+        if (p.sp_mode == SP_VEL_Z) {
+            row[(size_t)(job + 1) * p.n_rcv + c.idx] = __ldcg(J.tgt[0] + c.q);
+        } else {
+            const float s = __fadd_rn(__fadd_rn(__ldcg(J.tgt[0] + c.q), __ldcg(J.tgt[1] + c.q)),
+                                      __ldcg(J.tgt[2] + c.q));
+            row[c.idx] = __fdiv_rn(-s, 3.f);  // Eq. (3)
+        }
+    }
+}
+
 // warm L2 with a 128-byte line the epilogue will read (no registers held)
 __device__ __forceinline__ void prefetch_l2(const void* p)
 {
@@ -580,8 +639,8 @@ pass_strided(const __grid_constant__ PassParams p)
     }
     cp_async_commit_wait_all();
     __syncthreads();
-    if (!valid) return;
-    {
+    if (valid) {
+        // near part: the 10 taps in order from the first offset, then one add to the far part
         const int o = HALO + near_ofs(J.sign);
 #pragma unroll
         for (int q = 0; q < RA; ++q) {
@@ -596,14 +655,15 @@ pass_strided(const __grid_constant__ PassParams p)
             a[q].x = __fadd_rn(a[q].x, s.x);
             a[q].y = __fadd_rn(a[q].y, s.y);
         }
-    }
-    if (p.pdl == 1) pdl_wait();
+        if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
 #pragma unroll
-    for (int q = 0; q < RA; ++q) {
-        const int pos = j + q * BA;
-        if (p.axis == 1) y = pos; else z = pos;
-        epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y, off, soff);
+        for (int q = 0; q < RA; ++q) {
+            const int pos = j + q * BA;
+            if (p.axis == 1) y = pos; else z = pos;
+            epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y, off, soff);
+        }
     }
+    if (p.sp_mode != SP_NONE) special_phase(p, J, blockIdx.y);
 }
 
 // x pass epilogue: the far derivative from the turned-around FFT buffer (bf,
@@ -673,6 +733,8 @@ pass_x(const __grid_constant__ PassParams p)
     const int c = tid % CP, j = tid / CP;
     const PassJob& J = p.job[blockIdx.y];
     pdl_begin(p.pdl);
+    // the first pass of a fused time step advances the step counter
+    if (p.step_counter && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *p.step_counter += 1;
     const int nlines = p.ny * p.nz;
     const int sim = blockIdx.x % p.nsim;
     const size_t off = (size_t)sim * p.fstride, soff = (size_t)sim * p.sstride;

@@ -357,3 +357,65 @@ def test_smoothed_source_must_clear_the_pml(es):
             m.source_add_smoothed((7, 16, 16), synth.explosive(), w)  # its stencil would reach x = 5
         assert e.value.status == es.ES_ERR_ARG
         m.source_add_smoothed((8, 16, 16), synth.explosive(), w)
+
+
+def test_fused_sources_and_receivers_equal_the_separate_kernels(es, orc):
+    """With every axis on the FFT passes, point sources are injected and the
+    receivers recorded inside the passes (6 launches per step).  A smoothed
+    source of zero moment adds nothing but sends the run through the separate
+    injection and recording kernels (8 + 1 launches): traces and final state
+    agree bit for bit.  Two moment sources share a cell (their order matters),
+    a receiver sits on a source cell, and a point force is present; the fused
+    run also matches the oracle."""
+    shape = (32, 48, 64)
+    rho, cp, cs = synth.marine_model(shape=shape, seed=7)
+    dt = cfl_dt(cp, 10.0)
+    nt = 90
+    w = synth.ricker(nt, dt, 30.0)
+    srcs = [dict(kind="moment", pos=(30, 20, 15), m=synth.double_couple_sdr(30, 60, 90), w=w),
+            dict(kind="moment", pos=(30, 20, 15), m=synth.clvd(), w=0.5 * w),
+            dict(kind="force", pos=(40, 28, 17), m=(0.2, -1.0, 0.4), w=w * 1e7)]
+    with es.Model(rho, cp, cs, dx=10.0, pml=5) as m:
+        rcv = np.concatenate([m.seabed_receivers(4, 3), np.array([[30, 20, 15]], np.int32)])
+        out = []
+        for extra in (False, True):
+            m.state_reset()
+            m.source_clear()
+            for s in srcs:
+                if s["kind"] == "moment":
+                    m.source_add(s["pos"], s["m"], s["w"])
+                else:
+                    m.source_add_force(s["pos"], s["m"], s["w"])
+            if extra:
+                m.source_add_smoothed((32, 24, 16), np.zeros(6), w)
+            assert m.kernels_per_step() == (9 if extra else 6)
+            out.append((m.run(nt, dt, rcv), m.state_get()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    ref = orc.simulate(rho, cp, cs, dx=10.0, dt=dt, nt=nt, pml=5, sources=srcs, receivers=rcv)["traces"]
+    assert trace_errors(out[0][0], ref).max() < TOL
+
+
+def test_fused_batch_equals_separate_kernels(es):
+    """A batch of moment sources on FFT axes (fused) against the same batch
+    run one source at a time with a zero smoothed source beside it (the
+    separate kernels): equal bit for bit."""
+    shape = (32, 32, 48)
+    rho, cp, cs = synth.marine_model(shape=shape, seed=8)
+    dt, nt = cfl_dt(cp, 10.0), 60
+    rng = synth.SplitMix64(5)
+    box = synth.reservoir_box(shape, 4)
+    pos = synth.random_positions(rng, box, 3)
+    mts = np.array([synth.random_dc(rng) for _ in range(3)])
+    wav = np.stack([synth.ricker(nt, dt, 30.0)] * 3)
+    with es.Model(rho, cp, cs, dx=10.0, pml=4) as m:
+        rcv = m.seabed_receivers(3, 3)
+        m.batch_set(pos, mts, wav)
+        assert m.kernels_per_step() == 6
+        batched = m.run(nt, dt, rcv)
+    for b in range(3):
+        with es.Model(rho, cp, cs, dx=10.0, pml=4) as m1:
+            m1.source_set(pos[b], mts[b], wav[b])
+            m1.source_add_smoothed((24, 16, 10), np.zeros(6), wav[b])
+            assert m1.kernels_per_step() == 8
+            assert np.array_equal(m1.run(nt, dt, rcv), batched[b]), b
