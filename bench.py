@@ -592,7 +592,9 @@ def measure_paper(args):
                       "ms_per_step": ms, "s_per_source": round(ms * 1e-3, 3), "dtype": "f32",
                       "data": "synthetic",
                       "config": {"workload": "the paper's grid 125x75x301, 12.5/12.5/10 m, PML 10, "
-                                             f"{nt} steps, 105x55 seabed receivers, circulant passes"},
+                                             f"{nt} steps, 105x55 seabed receivers; x (125 = 5x5x5) and y (75 = 5x15) "
+                                             "through the FFT passes, z (301 = 7x43) through the circulant "
+                                             "passes"},
                       "paths": out}))
     return 0
 
@@ -658,7 +660,7 @@ def measure_configs(args):
                "Mcell_steps_per_s": round(float(n) * nt / (ms * 1e-3) / 1e6, 1)}
         if kind == "paper":
             # the paper's per-source times on this grid (2000 samples): K20 ~1313 s, C2075 ~2091 s
-            rec["passes"] = "circulant on all three axes (125, 75, 301 have no FFT plan)"
+            rec["passes"] = "x 125 (5x5x5) and y 75 (5x15) FFT, z 301 = 7 x 43 circulant"
             rec["s_per_source"] = round(ms * 1e-3, 3)
             rec["vs_paper_k20_s_per_source"] = round(1313.0 / (ms * 1e-3), 1)
         if name == "C1":

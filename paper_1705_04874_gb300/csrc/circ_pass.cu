@@ -33,7 +33,7 @@
 // (registers), 10 FP32 operations per multiply-add.
 #include <cstdlib>
 
-#include "circ_epilogue.cuh"
+#include "fft_pass.cuh"
 
 namespace es {
 namespace {

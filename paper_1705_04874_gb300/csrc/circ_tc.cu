@@ -38,7 +38,7 @@
 #include <algorithm>
 
 #include "es_internal.h"
-#include "circ_epilogue.cuh"
+#include "fft_pass.cuh"
 #include "tc_ptx.cuh"
 
 namespace es {

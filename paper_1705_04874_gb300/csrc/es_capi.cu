@@ -210,12 +210,12 @@ int ensure_prepared()
     return ES_OK;
 }
 
-// Axis lengths: an FFT plan (pass_kernels.cu), else the circulant pass up to
-// CIRC_MAX_N (circ_pass.cu).  The y and z FFT passes move x-adjacent pairs, so
-// they need an even nx; with an odd nx every axis takes the circulant pass.
+// Axis lengths: an FFT plan (pass_plans.h), else the circulant pass up to
+// CIRC_MAX_N (circ_pass.cu).  With an odd nx the y and z FFT passes move their
+// x-adjacent pencil pairs as single floats (pass_kernels_odd.cu).
 bool fft_plan(int n) { int a, b; return plan_radices(n, &a, &b) != 0; }
 bool axis_ok(int n) { return n >= 3 && n <= CIRC_MAX_N; }
-bool fft_axis(int n, int nx) { return fft_plan(n) && nx % 2 == 0; }
+bool fft_axis(int n, int) { return fft_plan(n); }
 
 // exp(-2 pi i m / n) and the staggered multipliers H = i kappa exp(sign i kappa d / 2) of
 // an axis, in FP64 then rounded.  The FFT passes evaluate D = N + far (es_internal.h):

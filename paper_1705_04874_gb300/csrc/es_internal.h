@@ -112,7 +112,7 @@ struct PassParams {
     int n_rcv;
 };
 
-// Plan of the two-stage FFT for an axis length (0 if unsupported).
+// Plan of the FFT for an axis length, as (R1, n / R1) (0 if unsupported).
 int plan_radices(int n, int* ra, int* rb);
 // Candidate plans for n (up to cap), and the plan in use per pass kind
 // (0 = x pass, 1 = y/z passes): read and select.
@@ -121,6 +121,10 @@ int plan_current(int kind, int n, int* ra, int* rb);
 int plan_select(int kind, int n, int ra, int rb);
 // Launches one pass (all jobs) along p.axis.  Returns a cudaError_t.
 cudaError_t launch_pass(const PassParams& p, cudaStream_t st);
+// The y / z FFT pass for an odd nx with stage radices ra, rb, rc (rc = 1: two
+// stages; pass_kernels_odd.cu), and its shared-memory opt-in.
+cudaError_t launch_strided_odd(int ra, int rb, int rc, dim3 grid, const PassParams& p, cudaStream_t st);
+cudaError_t prepare_strided_odd();
 // Longest axis the circulant pass takes (shared tiles of 2 x 32 x pad(n) floats).
 constexpr int CIRC_MAX_N = 512;
 // From this length on, the CUDA-core circulant passes along y and z run their epilogue from

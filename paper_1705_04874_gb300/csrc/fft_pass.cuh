@@ -22,7 +22,8 @@
 // Strided passes (y, z): a tile is 32 consecutive x (128-byte rows) by the
 // whole pencil; every global access of a warp is a full row segment.  The x
 // pass stages 32 whole x-lines (contiguous in memory) through shared memory
-// with float4 accesses and runs the same FFT core on the staged tile.
+// with float4 accesses (float accesses when the length is not a multiple of
+// 16) and runs the same FFT core on the staged tile.
 //
 // Each derivative is evaluated as a near part plus a far part (es_internal.h):
 // the multiplier tables hold H_far / n, and once the last inverse stage has
@@ -105,6 +106,27 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+
+// Packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2): two multiply-adds or adds
+// in one instruction, each component rounded exactly as fmaf / __fadd_rn
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+        "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+        "add.rn.f32x2 rd, ra, rb;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 
 // ---------------------------------------------------------------------------
 // forward DFTs of small sizes in registers: a[k] <- sum_j a[j] W_R^(jk)
@@ -191,7 +213,9 @@ template <> struct Dft<6> : DftPQ<2, 3> {};
 template <> struct Dft<8> : DftPQ<2, 4> {};
 template <> struct Dft<10> : DftPQ<2, 5> {};
 template <> struct Dft<12> : DftPQ<4, 3> {};
+template <> struct Dft<15> : DftPQ<3, 5> {};
 template <> struct Dft<16> : DftPQ<4, 4> {};
+template <> struct Dft<25> : DftPQ<5, 5> {};
 
 // ---------------------------------------------------------------------------
 // epilogues
@@ -325,6 +349,40 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
     }
 }
 
+// Epilogue for one cell (odd nx in the y / z passes, any length in the x pass,
+// the circulant passes): the same arithmetic as epilogue_pair / epilogue_quad,
+// one cell at a time.
+__device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos, int x, int y,
+                                             int z, float d, size_t off, size_t soff)
+{
+    if (J.kind == JOB_STORE) {
+        J.tgt[0][off + q] = d;
+        return;
+    }
+    const float dt = p.dt;
+    const bool slab = in_slab(pos, p.n, p.L);
+    const int S = 2 * p.L + 1;
+    if (J.kind == JOB_SINGLE) {
+        float inc = increment(dt, __ldg(J.coef[0] + q), d);
+        if (slab) {
+            const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
+            const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            inc = split_delta(J.slab[0], soff + si, P, inc);
+        }
+        atomicAdd(J.tgt[0] + off + q, inc);
+    } else {
+        const float lam = __ldg(J.coef[0] + q), mu = __ldg(J.coef[1] + q);
+        const float P = slab ? __ldg(p.pc + pos) : 1.f;
+        const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            float inc = increment(dt, normal_coef(lam, mu, t == J.diag), d);
+            if (slab) inc = split_delta(J.slab[t], soff + si, P, inc);
+            atomicAdd(J.tgt[t] + off + q, inc);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FFT core on the shared [pos][line] layout (one buffer, updated in place:
 // every stage reads all its inputs, the block synchronises, then it writes)
@@ -405,13 +463,141 @@ struct Core {
         stageA_inv_load(buf, tw, a, j, c);
         stageA_inv_finish(a);
     }
+
+    // everything between the first forward and the last inverse stage
+    static __device__ __forceinline__ void middle(float2* buf, const float2* tw, const float2* H, int j, int c)
+    {
+        float2 v[MB][RB];
+        stageB_compute(buf, v, tw, H, j, c);
+        __syncthreads();
+        stageB_store(buf, v, j, c);
+    }
 };
+
+// Three-stage plan n = R1 R2 R3 (Stockham, as Core): forward stages of radix
+// R1, R2, R3, the spectral multiply on the elements the last one leaves in a
+// thread's registers, then the inverse (forward DFTs of the conjugate) with
+// the radices reversed: R3 on those same elements, R2, and R1, which ends on
+// the elements j + q n/R1 the first stage read.  A stage of radix R after
+// stages whose radices multiply to Ns: butterfly b (k = b mod Ns) reads
+// elements b + r n/R times W_(Ns R)^(k r), runs the R-point DFT and writes
+// element (b / Ns) Ns R + k + q Ns.  All stages but the first and the last
+// run on the shared buffer; n/R1 threads per line, every butterfly of a
+// stage by one thread.
+template <int R1, int R2, int R3, int CPAD>
+struct Core3 {
+    static constexpr int N = R1 * R2 * R3;
+    static constexpr int BA = N / R1;  // first / last stage butterflies = threads per line
+    static constexpr int T = BA;
+
+    static __device__ __forceinline__ void stageA_store(const float2* a, float2* buf, int j, int c)
+    {
+#pragma unroll
+        for (int q = 0; q < R1; ++q) buf[(j * R1 + q) * CPAD + c] = a[q];
+    }
+
+    // one stage of radix R after radices multiplying to NS, shared buffer to
+    // shared buffer (reads, block barrier, writes)
+    template <int R, int NS>
+    static __device__ __forceinline__ void stage(float2* buf, const float2* tw, int j, int c)
+    {
+        constexpr int B = N / R, M = (B + T - 1) / T, TS = N / (NS * R);
+        float2 v[M][R];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int b = j + m * T;
+            if (B % T == 0 || b < B) {
+                const int k = b % NS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 x = buf[(b + r * B) * CPAD + c];
+                    v[m][r] = r == 0 ? x : cmul(x, tw[k * r * TS]);
+                }
+                Dft<R>::run(v[m]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int b = j + m * T;
+            if (B % T == 0 || b < B) {
+                const int k = b % NS, o = (b / NS) * NS * R + k;
+#pragma unroll
+                for (int q = 0; q < R; ++q) buf[(o + q * NS) * CPAD + c] = v[m][q];
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void middle(float2* buf, const float2* tw, const float2* H, int j, int c)
+    {
+        stage<R2, R1>(buf, tw, j, c);
+        __syncthreads();
+        {
+            // last forward stage (radix R3, Ns = n/R3, so k = b), multiply,
+            // conjugate, first inverse stage (radix R3, Ns = 1) in registers
+            constexpr int B = N / R3, M = (B + T - 1) / T;
+            float2 v[M][R3];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int b = j + m * T;
+                if (B % T == 0 || b < B) {
+#pragma unroll
+                    for (int r = 0; r < R3; ++r) {
+                        const float2 x = buf[(b + r * B) * CPAD + c];
+                        v[m][r] = r == 0 ? x : cmul(x, tw[b * r]);
+                    }
+                    Dft<R3>::run(v[m]);
+#pragma unroll
+                    for (int q = 0; q < R3; ++q) {
+                        const float2 y = cmul(H[b + q * B], v[m][q]);
+                        v[m][q] = make_float2(y.x, -y.y);
+                    }
+                    Dft<R3>::run(v[m]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int b = j + m * T;
+                if (B % T == 0 || b < B) {
+#pragma unroll
+                    for (int q = 0; q < R3; ++q) buf[(b * R3 + q) * CPAD + c] = v[m][q];
+                }
+            }
+        }
+        __syncthreads();
+        stage<R2, R3>(buf, tw, j, c);
+    }
+
+    // last inverse stage (radix R1, Ns = n/R1, so k = j); a[q] = conj(result)
+    // at element j + q BA
+    static __device__ __forceinline__ void stageA_inv(const float2* buf, const float2* tw, float2* a, int j, int c)
+    {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const float2 x = buf[(j + r * BA) * CPAD + c];
+            a[r] = r == 0 ? x : cmul(x, tw[j * r]);
+        }
+        Dft<R1>::run(a);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) a[q].y = -a[q].y;
+    }
+};
+
+// the FFT core of a plan (RC = 1: two stages)
+template <int RA, int RB, int RC, int CPAD>
+using CoreOf = std::conditional_t<RC == 1, Core<RA, RB, CPAD>, Core3<RA, RB, RC, CPAD>>;
 
 // asynchronous 8-byte global -> shared copy (cp.async, through L1); no
 // register is held while it is in flight
 __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
                  "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit_wait_all()
@@ -421,14 +607,15 @@ __device__ __forceinline__ void cp_async_commit_wait_all()
 
 constexpr int CP = 16;  // complex lines (pencil pairs) per CTA
 
-template <int RA, int RB>
-__host__ __device__ constexpr int pass_threads() { return (RA * RB / RA) * CP; }
+template <int RA, int RB, int RC>
+__host__ __device__ constexpr int pass_threads() { return RB * RC * CP; }
 
-// blocks per SM the register budget is sized for (about 1024 threads per SM)
-template <int RA, int RB>
+// blocks per SM the register budget is sized for (about 1024 threads per SM;
+// 1200 for the three-stage plans, whose butterflies hold fewer registers)
+template <int RA, int RB, int RC>
 __host__ __device__ constexpr int pass_min_blocks()
 {
-    return pass_threads<RA, RB>() >= 1024 ? 1 : 1024 / pass_threads<RA, RB>();
+    return pass_threads<RA, RB, RC>() >= 1024 ? 1 : (RC == 1 ? 1024 : 1200) / pass_threads<RA, RB, RC>();
 }
 
 // rows of wrap-around copies on each side of the strided passes' reloaded
@@ -437,16 +624,27 @@ constexpr int HALO = 5;
 static_assert(-near_ofs(-1) <= HALO && near_ofs(+1) + NEAR_TAPS - 1 <= HALO, "near taps reach beyond the halo");
 
 // shared bytes: one buffer [N + 2 HALO][CP] (FFT, then the source tile) + tables (y, z passes)
-template <int RA, int RB>
+template <int RA, int RB, int RC>
 __host__ __device__ constexpr size_t pass_smem_strided()
 {
-    return sizeof(float2) * ((size_t)(RA * RB + 2 * HALO) * CP + 3 * (size_t)RA * RB);
+    return sizeof(float2) * ((size_t)(RA * RB * RC + 2 * HALO) * CP + 3 * (size_t)RA * RB * RC);
 }
-// FFT buffer [N][CP + 1] + tables (x pass)
-template <int RA, int RB>
+// x pass, lengths that are not a multiple of 16: cells per near-stencil item
+// (a divisor of n) and the halo of the per-line copy of the source tile
+template <int N>
+__host__ __device__ constexpr int xseg()
+{
+    return N % 5 == 0 ? 5 : (N % 4 == 0 ? 4 : (N % 3 == 0 ? 3 : (N % 2 == 0 ? 2 : 1)));
+}
+constexpr int XHALO = 5;
+// FFT buffer [N][CP + 1] + tables (x pass); for a length that is not a
+// multiple of 16 also the source tile, line by line with XHALO wrap-around
+// copies on each side
+template <int RA, int RB, int RC>
 __host__ __device__ constexpr size_t pass_smem_x()
 {
-    return sizeof(float2) * ((size_t)RA * RB * (CP + 1) + 3 * (size_t)RA * RB);
+    constexpr size_t N = (size_t)RA * RB * RC;
+    return sizeof(float2) * (N * (CP + 1) + 3 * N) + (N % 16 ? sizeof(float) * 2 * CP * (N + 2 * XHALO) : 0);
 }
 
 // Programmatic dependent launch (a pass launched with PDL while the previous
@@ -564,12 +762,14 @@ __device__ __forceinline__ void load_tables(const PassParams& p, float2* s_tw, f
 }
 
 // y and z passes: blockIdx.x = tile (32 consecutive x at one z (y pass) or
-// one y (z pass)), blockIdx.y = job
-template <int RA, int RB>
-__global__ void __launch_bounds__(pass_threads<RA, RB>(), pass_min_blocks<RA, RB>())
+// one y (z pass)), blockIdx.y = job.  ODD: nx is odd, so a pencil pair does not
+// start on an 8-byte boundary in every row; the pair then moves as two floats
+// (the second one absent at x = nx - 1), with the same arithmetic.
+template <int RA, int RB, int RC, bool ODD>
+__global__ void __launch_bounds__(pass_threads<RA, RB, RC>(), pass_min_blocks<RA, RB, RC>())
 pass_strided(const __grid_constant__ PassParams p)
 {
-    using C = Core<RA, RB, CP>;
+    using C = CoreOf<RA, RB, RC, CP>;
     constexpr int N = C::N, BA = C::BA, T = C::T;
     extern __shared__ float2 smem[];
     float2* buf = smem;  // FFT rows 0 .. N-1; then the source tile at rows HALO + pos (wrapped)
@@ -588,6 +788,7 @@ pass_strided(const __grid_constant__ PassParams p)
     const int tx = tile % ntx, outer = tile / ntx;
     const int x = tx * 2 * CP + 2 * c;
     const bool valid = x < p.nx;
+    const bool valid1 = x + 1 < p.nx;  // the second pencil of the pair (ODD)
     size_t base, est;
     int y = 0, z = 0;
     if (p.axis == 1) {
@@ -601,10 +802,19 @@ pass_strided(const __grid_constant__ PassParams p)
     }
     const float* src = J.src + off + base;
     float2 a[RA];
+    if constexpr (ODD) {
 #pragma unroll
-    for (int r = 0; r < RA; ++r)
-        a[r] = valid ? __ldg(reinterpret_cast<const float2*>(src + (size_t)(j + r * BA) * est))
-                     : make_float2(0.f, 0.f);
+        for (int r = 0; r < RA; ++r) {
+            const float* g = src + (size_t)(j + r * BA) * est;
+            a[r].x = valid ? __ldg(g) : 0.f;
+            a[r].y = valid1 ? __ldg(g + 1) : 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RA; ++r)
+            a[r] = valid ? __ldg(reinterpret_cast<const float2*>(src + (size_t)(j + r * BA) * est))
+                         : make_float2(0.f, 0.f);
+    }
     // coefficient rows of this tile (128 bytes each) into L2 for the epilogue
     if (tid < N && J.coef[0] && tx * 2 * CP < p.nx) {
         const size_t row = base - 2 * c + (size_t)tid * est;
@@ -615,12 +825,7 @@ pass_strided(const __grid_constant__ PassParams p)
     Dft<RA>::run(a);
     C::stageA_store(a, buf, j, c);
     __syncthreads();
-    {
-        float2 v[C::MB][RB];
-        C::stageB_compute(buf, v, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
-        __syncthreads();
-        C::stageB_store(buf, v, j, c);
-    }
+    C::middle(buf, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
     __syncthreads();
     C::stageA_inv(buf, s_tw, a, j, c);
     __syncthreads();
@@ -629,13 +834,30 @@ pass_strided(const __grid_constant__ PassParams p)
         float2* sb = buf + (j + HALO) * CP + c;
         const size_t gstep = (size_t)BA * est;
 #pragma unroll 1
-        for (int r = 0; r < RA; ++r, g += gstep, sb += BA * CP) cp_async8(sb, g);
+        for (int r = 0; r < RA; ++r, g += gstep, sb += BA * CP) {
+            if constexpr (ODD) {
+                cp_async4(&sb->x, g);
+                if (valid1) cp_async4(&sb->y, g + 1);
+                else sb->y = 0.f;
+            } else {
+                cp_async8(sb, g);
+            }
+        }
     }
     for (int i = tid; i < 2 * HALO * CP; i += T * CP) {
         const int h = i / CP, cc = i % CP;
-        if (tx * 2 * CP + 2 * cc >= p.nx) continue;
+        const int xc = tx * 2 * CP + 2 * cc;
+        if (xc >= p.nx) continue;
         const int pos = h < HALO ? N - HALO + h : h - HALO;
-        cp_async8(buf + (h < HALO ? h : N + h) * CP + cc, J.src + off + base - 2 * c + 2 * cc + (size_t)pos * est);
+        float2* d = buf + (h < HALO ? h : N + h) * CP + cc;
+        const float* g = J.src + off + base - 2 * c + 2 * cc + (size_t)pos * est;
+        if constexpr (ODD) {
+            cp_async4(&d->x, g);
+            if (xc + 1 < p.nx) cp_async4(&d->y, g + 1);
+            else d->y = 0.f;
+        } else {
+            cp_async8(d, g);
+        }
     }
     cp_async_commit_wait_all();
     __syncthreads();
@@ -647,20 +869,21 @@ pass_strided(const __grid_constant__ PassParams p)
             const float2* w = buf + (j + q * BA + o) * CP + c;
             float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int t = 0; t < NEAR_TAPS; ++t) {
-                const float2 v = w[t * CP];
-                s.x = fmaf(J.g[t], v.x, s.x);
-                s.y = fmaf(J.g[t], v.y, s.y);
-            }
-            a[q].x = __fadd_rn(a[q].x, s.x);
-            a[q].y = __fadd_rn(a[q].y, s.y);
+            for (int t = 0; t < NEAR_TAPS; ++t) s = fma2(make_float2(J.g[t], J.g[t]), w[t * CP], s);
+            a[q] = add2(a[q], s);
         }
         if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
 #pragma unroll
         for (int q = 0; q < RA; ++q) {
             const int pos = j + q * BA;
             if (p.axis == 1) y = pos; else z = pos;
-            epilogue_pair(p, J, base + (size_t)pos * est, pos, x, y, z, a[q].x, a[q].y, off, soff);
+            const size_t qc = base + (size_t)pos * est;
+            if constexpr (ODD) {
+                epilogue_one(p, J, qc, pos, x, y, z, a[q].x, off, soff);
+                if (valid1) epilogue_one(p, J, qc + 1, pos, x + 1, y, z, a[q].y, off, soff);
+            } else {
+                epilogue_pair(p, J, qc, pos, x, y, z, a[q].x, a[q].y, off, soff);
+            }
         }
     }
     if (p.sp_mode != SP_NONE) special_phase(p, J, blockIdx.y);
@@ -699,15 +922,140 @@ __device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJ
             w[4 * m + 2] = v.z;
             w[4 * m + 3] = v.w;
         }
+        // outputs xx, xx + 1 and xx + 2, xx + 3 as packed pairs
+        float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < NEAR_TAPS; ++t) {
+            const float2 g2 = make_float2(J.g[t], J.g[t]);
+            s01 = fma2(g2, make_float2(w[8 + OFS + t], w[9 + OFS + t]), s01);
+            s23 = fma2(g2, make_float2(w[10 + OFS + t], w[11 + OFS + t]), s23);
+        }
+        const float sn[4] = {s01.x, s01.y, s23.x, s23.y};
         float d[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float s = 0.f;
-#pragma unroll
-            for (int t = 0; t < NEAR_TAPS; ++t) s = fmaf(J.g[t], w[8 + e + OFS + t], s);
-            d[e] = __fadd_rn(bf[((xx + e) * CPAD) * 2 + r], s);
-        }
+        for (int e = 0; e < 4; ++e) d[e] = __fadd_rn(bf[((xx + e) * CPAD) * 2 + r], sn[e]);
         epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d, off, soff);
+    }
+}
+
+// Epilogue for 4 consecutive cells of an x-pass tile in memory order (f0 =
+// the first one's offset from the tile start, q0 its linear index, 16-byte
+// aligned): a chunk may span two lines, so every cell takes its own x and
+// line for the PML split (slab row S line); the arithmetic of epilogue_one.
+template <int N>
+__device__ __forceinline__ void epilogue_quad_flat(const PassParams& p, const PassJob& J, size_t q0, int f0,
+                                                   int line0, float4 d4, size_t off, size_t soff)
+{
+    if (J.kind == JOB_STORE) {
+        *reinterpret_cast<float4*>(J.tgt[0] + off + q0) = d4;
+        return;
+    }
+    const float d[4] = {d4.x, d4.y, d4.z, d4.w};
+    const float dt = p.dt;
+    const int S = 2 * p.L + 1;
+    int xs[4];
+    size_t srow[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int r = (f0 + e) / N;
+        xs[e] = f0 + e - r * N;
+        srow[e] = soff + (size_t)S * (size_t)(line0 + r);
+    }
+    if (J.kind == JOB_SINGLE) {
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+        float iv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            iv[e] = increment(dt, cv[e], d[e]);
+            if (in_slab(xs[e], p.n, p.L))
+                iv[e] = split_delta(J.slab[0], srow[e] + slab_pos(xs[e], p.n, p.L),
+                                    __ldg((J.stag ? p.ps : p.pc) + xs[e]), iv[e]);
+        }
+        atomicAdd(reinterpret_cast<float4*>(J.tgt[0] + off + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
+    } else {
+        const float4 l4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
+        const float4 m4 = __ldg(reinterpret_cast<const float4*>(J.coef[1] + q0));
+        const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+        const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            float iv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                iv[e] = increment(dt, normal_coef(lv[e], mv[e], t == J.diag), d[e]);
+                if (in_slab(xs[e], p.n, p.L))
+                    iv[e] = split_delta(J.slab[t], srow[e] + slab_pos(xs[e], p.n, p.L), __ldg(p.pc + xs[e]), iv[e]);
+            }
+            atomicAdd(reinterpret_cast<float4*>(J.tgt[t] + off + q0), make_float4(iv[0], iv[1], iv[2], iv[3]));
+        }
+    }
+}
+
+// x pass epilogue for a length that is not a multiple of 16.  The derivative
+// of every cell is formed one cell per thread in memory order over the tile
+// (the far part from the turned-around buffer, the near taps read one by one
+// and wrapped along the line: the arithmetic of pass_x_epilogue), written
+// back to the buffer in memory order, and the update then takes four cells
+// per thread with 16-byte coefficient loads and reductions (the tile, 32 n
+// floats from line 32 k, starts on a 16-byte boundary).
+template <int N, int CPAD, int OFS, int NT>
+__device__ __forceinline__ void pass_x_epilogue_any(const PassParams& p, const PassJob& J, float* bf,
+                                                    const float* srcs, int line0, int nlines, size_t off,
+                                                    size_t soff)
+{
+    static_assert(XHALO + OFS >= 0 && XHALO + OFS + NEAR_TAPS - 1 <= 2 * XHALO, "near taps outside the halo");
+    constexpr int LINES = 2 * CP;
+    constexpr int XS = xseg<N>(), NS = N / XS, W = N + 2 * XHALO;
+    constexpr int ITER = (LINES * NS + NT - 1) / NT;
+    static_assert(LINES * N <= 2 * N * CPAD, "the tile's derivatives fit the buffer");
+    const int nl = min(LINES, nlines - line0);
+    const int nf = nl * N;
+    const int tid = threadIdx.x;
+    // item = XS consecutive cells of one line: a window of XS + NEAR_TAPS - 1
+    // source values from the line's copy, the near taps in order from the
+    // first offset, then one add to the far part
+    float dv[ITER][XS];
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int it = tid + i * NT;
+        const int r = it / NS, x0 = (it - r * NS) * XS;
+        if (r < nl) {
+            const float* wrow = srcs + r * W + XHALO + OFS + x0;
+            float w[XS + NEAR_TAPS - 1];
+#pragma unroll
+            for (int k = 0; k < XS + NEAR_TAPS - 1; ++k) w[k] = wrow[k];
+#pragma unroll
+            for (int e = 0; e < XS; ++e) {
+                float s = 0.f;
+#pragma unroll
+                for (int t = 0; t < NEAR_TAPS; ++t) s = fmaf(J.g[t], w[e + t], s);
+                dv[i][e] = __fadd_rn(bf[((x0 + e) * CPAD) * 2 + r], s);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int it = tid + i * NT;
+        const int r = it / NS, x0 = (it - r * NS) * XS;
+        if (r < nl) {
+#pragma unroll
+            for (int e = 0; e < XS; ++e) bf[r * N + x0 + e] = dv[i][e];
+        }
+    }
+    __syncthreads();
+    const size_t q0 = (size_t)line0 * N;
+    // 16-byte chunks need a 16-byte aligned simulation offset too (an odd cell
+    // count per simulation leaves every other one unaligned)
+    const int nq = (off & 3) == 0 ? nf / 4 : 0;
+    for (int i = tid; i < nq; i += NT)
+        epilogue_quad_flat<N>(p, J, q0 + 4 * (size_t)i, 4 * i, line0, reinterpret_cast<const float4*>(bf)[i], off,
+                              soff);
+    // what is left: a last, partial tile's cells past its last full chunk
+    for (int f = 4 * nq + tid; f < nf; f += NT) {
+        const int r = f / N, x = f - r * N, line = line0 + r;
+        epilogue_one(p, J, q0 + f, x, x, line % p.ny, line / p.ny, bf[f], off, soff);
     }
 }
 
@@ -715,15 +1063,15 @@ __device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJ
 // the tile is one contiguous block of memory), blockIdx.y = job.  The FFT
 // result is turned around in the shared buffer so that a thread owns four
 // consecutive x of one line (an item) in the epilogue.
-template <int RA, int RB>
-__global__ void __launch_bounds__(pass_threads<RA, RB>(), pass_min_blocks<RA, RB>())
+template <int RA, int RB, int RC>
+__global__ void __launch_bounds__(pass_threads<RA, RB, RC>(), pass_min_blocks<RA, RB, RC>())
 pass_x(const __grid_constant__ PassParams p)
 {
     constexpr int CPAD = CP + 1;  // row padding: the staging transposes stay conflict-free
-    using C = Core<RA, RB, CPAD>;
+    using C = CoreOf<RA, RB, RC, CPAD>;
     constexpr int N = C::N, BA = C::BA, NT = C::T * CP;
     constexpr int LINES = 2 * CP;
-    constexpr int ITEMS = LINES * N / 4;  // float4 chunks in the tile
+    constexpr int ITEMS = LINES * N / 4;  // float4 chunks in the tile (N a multiple of 16)
     extern __shared__ float2 smem[];
     float2* buf = smem;
     float2* s_tw = buf + N * CPAD;
@@ -751,17 +1099,41 @@ pass_x(const __grid_constant__ PassParams p)
             if (J.coef[1]) prefetch_l2(J.coef[1] + off);
         }
     }
+    if constexpr (N % 16 == 0) {
 #pragma unroll
-    for (int it = tid; it < ITEMS; it += NT) {
-        const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
-        const int xx = (hi * 4 + lo) * 4;
-        const int line = line0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(src + (size_t)line * N + xx));
-        bf[((xx + 0) * CPAD) * 2 + r] = v.x;
-        bf[((xx + 1) * CPAD) * 2 + r] = v.y;
-        bf[((xx + 2) * CPAD) * 2 + r] = v.z;
-        bf[((xx + 3) * CPAD) * 2 + r] = v.w;
+        for (int it = tid; it < ITEMS; it += NT) {
+            const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
+            const int xx = (hi * 4 + lo) * 4;
+            const int line = line0 + r;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(src + (size_t)line * N + xx));
+            bf[((xx + 0) * CPAD) * 2 + r] = v.x;
+            bf[((xx + 1) * CPAD) * 2 + r] = v.y;
+            bf[((xx + 2) * CPAD) * 2 + r] = v.z;
+            bf[((xx + 3) * CPAD) * 2 + r] = v.w;
+        }
+    } else {
+        // any length: the tile is one contiguous run of 32 N floats, read in
+        // order; each value also goes to the per-line source copy (row r at
+        // r (N + 2 XHALO), x at XHALO + x, the ends wrapped on both sides)
+        const float* tile = src + (size_t)line0 * N;
+        const int nf = min(LINES, nlines - line0) * N;
+        float* srcs = reinterpret_cast<float*>(s_hm + N);
+        constexpr int W = N + 2 * XHALO;
+        constexpr int ITER = (LINES * N + NT - 1) / NT;
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int f = tid + i * NT;
+            if (f < LINES * N) {
+                const int r = f / N, xx = f - r * N;
+                const float v = f < nf ? __ldg(tile + f) : 0.f;
+                bf[(xx * CPAD) * 2 + r] = v;
+                float* row = srcs + r * W + XHALO;
+                row[xx] = v;
+                if (xx < XHALO) row[N + xx] = v;
+                if (xx >= N - XHALO) row[xx - N] = v;
+            }
+        }
     }
     load_tables<N>(p, s_tw, s_hp, s_hm, tid, NT);
     __syncthreads();
@@ -772,12 +1144,7 @@ pass_x(const __grid_constant__ PassParams p)
     __syncthreads();
     C::stageA_store(a, buf, j, c);
     __syncthreads();
-    {
-        float2 v[C::MB][RB];
-        C::stageB_compute(buf, v, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
-        __syncthreads();
-        C::stageB_store(buf, v, j, c);
-    }
+    C::middle(buf, s_tw, J.sign > 0 ? s_hp : s_hm, j, c);
     __syncthreads();
     C::stageA_inv(buf, s_tw, a, j, c);
     __syncthreads();
@@ -785,8 +1152,14 @@ pass_x(const __grid_constant__ PassParams p)
     for (int q = 0; q < RA; ++q) buf[(j + q * BA) * CPAD + c] = a[q];
     __syncthreads();
     if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
-    if (J.sign > 0) pass_x_epilogue<N, CPAD, near_ofs(+1)>(p, J, bf, src, line0, nlines, off, soff);
-    else pass_x_epilogue<N, CPAD, near_ofs(-1)>(p, J, bf, src, line0, nlines, off, soff);
+    if constexpr (N % 16 == 0) {
+        if (J.sign > 0) pass_x_epilogue<N, CPAD, near_ofs(+1)>(p, J, bf, src, line0, nlines, off, soff);
+        else pass_x_epilogue<N, CPAD, near_ofs(-1)>(p, J, bf, src, line0, nlines, off, soff);
+    } else {
+        const float* srcs = reinterpret_cast<const float*>(s_hm + N);
+        if (J.sign > 0) pass_x_epilogue_any<N, CPAD, near_ofs(+1), NT>(p, J, bf, srcs, line0, nlines, off, soff);
+        else pass_x_epilogue_any<N, CPAD, near_ofs(-1), NT>(p, J, bf, srcs, line0, nlines, off, soff);
+    }
 }
 
 }  // namespace es

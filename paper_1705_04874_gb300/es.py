@@ -218,9 +218,12 @@ def es_fft_plan_select(pass_kind, n, ra, rb):
     _check(_load().es_fft_plan_select(int(pass_kind), int(n), int(ra), int(rb)), "es_fft_plan_select")
 
 
+# FFT plans per axis length, named (R1, n / R1); the first is the default.  (3, 25)
+# and (5, 25) run as three stages (3 x 5 x 5, 5 x 5 x 5).
 PLAN_CANDIDATES = {16: [(4, 4)], 32: [(8, 4), (4, 8)], 48: [(12, 4), (4, 12)], 64: [(16, 4), (8, 8), (4, 16)],
-                   80: [(16, 5), (5, 16)], 96: [(16, 6), (6, 16)], 128: [(16, 8), (8, 16)],
-                   160: [(16, 10), (10, 16)], 192: [(16, 12), (12, 16)], 256: [(16, 16)]}
+                   75: [(5, 15), (3, 25), (15, 5)], 80: [(16, 5), (5, 16)], 96: [(16, 6), (6, 16)],
+                   125: [(5, 25), (25, 5)], 128: [(16, 8), (8, 16)], 160: [(16, 10), (10, 16)],
+                   192: [(16, 12), (12, 16)], 256: [(16, 16)]}
 
 
 def es_derivative(f, axis, d, shift, out, stream=None):

@@ -101,3 +101,28 @@ def test_fault_injection_switch_without_a_gpu(lib):
     assert lib.es_model_create(None, None, None, 32, 32, 32, 10.0, 6, ctypes.byref(h)) == es.ES_ERR_ARG
     lib.es_fault_inject_alloc(0)
     assert lib.es_debug_live_allocations() == live
+
+
+def test_fft_plan_table_without_a_gpu(lib):
+    """The plan table is host-side: every length of the binding's candidate list
+    has its first candidate as the default for both pass kinds, every other
+    candidate can be selected, and a length without a plan (among them the
+    paper's 301 = 7 x 43) answers ES_ERR_SIZE."""
+    from paper_1705_04874_gb300 import es
+    ra, rb = ctypes.c_int(), ctypes.c_int()
+    for n in range(1, 513):
+        for kind in (0, 1):
+            rc = lib.es_fft_plan(kind, n, ctypes.byref(ra), ctypes.byref(rb))
+            if n in es.PLAN_CANDIDATES:
+                assert rc == es.ES_OK and (ra.value, rb.value) == es.PLAN_CANDIDATES[n][0], n
+                assert ra.value * rb.value == n
+            else:
+                assert rc == es.ES_ERR_SIZE, n
+    for n, cands in es.PLAN_CANDIDATES.items():
+        for kind in (0, 1):
+            for c in cands[::-1]:
+                assert lib.es_fft_plan_select(kind, n, *c) == es.ES_OK
+                assert lib.es_fft_plan(kind, n, ctypes.byref(ra), ctypes.byref(rb)) == es.ES_OK
+                assert (ra.value, rb.value) == c
+            assert lib.es_fft_plan_select(kind, n, n, 1) == es.ES_ERR_SIZE
+    assert lib.es_fft_plan_select(2, 64, 8, 8) == es.ES_ERR_ARG

@@ -1,8 +1,9 @@
 """Axis lengths without an FFT plan -- odd or non-smooth, 3 to 512, among them
-the paper's own 125 x 75 x 301 grid with 12.5 / 12.5 / 10 m spacing (Sec. III):
-the circulant passes against the FP64 oracle, through the C ABI.  Single
-derivatives on every axis, full runs on an all-odd grid and on a grid that
-mixes FFT and circulant axes, the paper's grid itself, and batching."""
+the z axis of the paper's own 125 x 75 x 301 grid with 12.5 / 12.5 / 10 m
+spacing (Sec. III; 301 = 7 x 43): the circulant passes against the FP64
+oracle, through the C ABI.  Single derivatives on every axis, full runs on an
+all-odd grid and on a grid that mixes FFT and circulant axes, the paper's grid
+itself, and batching."""
 import numpy as np
 import pytest
 
@@ -24,8 +25,8 @@ def es():
     return _es
 
 
-# [nz][ny][nx]: odd nx (every axis circulant), even nx with odd ny or nz
-# (FFT and circulant axes side by side), the shortest (3) and longest (512) axes
+# [nz][ny][nx]: circulant axes beside FFT axes (75 and 125 have plans), with
+# odd and even nx; the shortest (3) and longest (512) axes
 SHAPES = [(18, 20, 125), (301, 4, 32), (5, 75, 36), (3, 7, 9), (12, 10, 512), (40, 33, 17)]
 
 
@@ -95,8 +96,9 @@ def test_mixed_fft_and_circulant_axes(es, orc):
 
 
 def test_paper_grid_matches_oracle(es, orc):
-    """The paper's grid: 125 x 75 x 301 cells, dx = dy = 12.5 m, dz = 10 m,
-    10-cell PML, 57 water cells, a double couple in the reservoir box; 12 steps
+    """The paper's grid: 125 x 75 x 301 cells, dx = dy = 12.5 m, dz = 10 m (x
+    and y through the FFT plans 5 x 25 and 5 x 15, z circulant), 10-cell PML,
+    57 water cells, a double couple in the reservoir box; 12 steps
     of every field against the oracle, and the seabed receivers at the depth
     where cs first turns nonzero."""
     shape = (301, 75, 125)

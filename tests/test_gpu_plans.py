@@ -22,11 +22,14 @@ def es():
             _es.es_fft_plan_select(kind, n, *cands[0])
 
 
-@pytest.mark.parametrize("n", [32, 48, 64, 80, 96, 128, 160, 192])
+@pytest.mark.parametrize("n", [32, 48, 64, 75, 80, 96, 125, 128, 160, 192])
 def test_every_plan_matches_oracle(es, orc, n):
+    """Along x, and along y and z with an even and an odd nx (the y / z passes
+    move pencil pairs as float2 or, for an odd nx, as two floats)."""
     import torch
     rng = np.random.default_rng(n)
-    for axis, shape in ((0, (16, 32, n)), (1, (16, n, 32)), (2, (n, 16, 32))):
+    for axis, shape in ((0, (16, 32, n)), (1, (16, n, 32)), (2, (n, 16, 32)), (1, (16, n, 33)),
+                        (2, (n, 16, 45))):
         f = rng.standard_normal(shape).astype(np.float32)
         ref = orc.deriv(f.astype(np.float64), axis, 10.0, +1)
         kind = 0 if axis == 0 else 1
