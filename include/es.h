@@ -240,7 +240,9 @@ int es_seabed_receivers(const es_model* m, int rx, int ry, int* rcv);
  * D(+/-) f (x) = f'(x +/- d/2), i.e. forward FFT along the axis, multiply by
  * i kappa exp(+/- i kappa d / 2), inverse FFT, with kappa_m = 2 pi m / (n d),
  * m = -n/2 .. n/2 - 1.  The same fused FFT pass kernels as es_run.  f, out:
- * [nz][ny][nx] device pointers (distinct); shift = +1 or -1. */
+ * [nz][ny][nx] device pointers (distinct), each on a 16-byte boundary (the
+ * passes move 8- and 16-byte vectors; ES_ERR_ARG otherwise); shift = +1 or
+ * -1. */
 int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, int shift, float* out,
                   void* stream);
 
@@ -249,14 +251,16 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
  * out = sum over the axes of D(+) D(-) f, which multiplies every wavenumber
  * bin by -kappa^2 (Nyquist included): the spectral Laplacian, with the
  * solver's own derivative passes.  f, out: [nz][ny][nx] device arrays
- * (distinct), spacings dx, dy, dz > 0.  Allocates 2 n floats of scratch. */
+ * (distinct, each on a 16-byte boundary, else ES_ERR_ARG), spacings dx, dy,
+ * dz > 0.  Allocates about 2 n floats of scratch. */
 int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, double dz, float* out,
                  void* stream);
 
 /* FFT plan autotuner: for each axis length of this model with more than one
- * two-stage plan (radix order R1 x R2), times the model's own velocity and
- * stress passes (reps launches after one warm-up, CUDA events on the model's
- * stream) with every candidate, keeps the fastest per pass kind (x pass, y/z
+ * plan (radix order R1 x R2, or three stages R1 x R2 x R3; a plan is named
+ * (R1, n / R1)), times the model's own velocity and stress passes (reps
+ * launches after one warm-up, CUDA events on the model's stream) with every
+ * candidate, keeps the fastest per pass kind (x pass, y/z
  * passes) and length for the rest of the process, and records the choice
  * in the plan cache ($ES_TUNE_CACHE, else $HOME/.cache/es_fft_plans.txt,
  * keyed by device name), which every process loads when it creates its first
@@ -264,11 +268,15 @@ int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, d
  * per candidate. */
 int es_model_autotune(es_model* m, int reps, char* report, int report_len);
 
-/* The plan in use for pass kind 0 (x) or 1 (y/z) and axis length n. */
+/* The plan in use for pass kind 0 (x) or 1 (y/z) and axis length n, as
+ * ra = R1 (the first stage's radix) and rb = n / R1: (5, 25) for 125 is the
+ * three-stage 5 x 5 x 5, (3, 25) for 75 the three-stage 3 x 5 x 5.  Host-side
+ * only; ES_ERR_SIZE if n has no plan. */
 int es_fft_plan(int pass_kind, int n, int* ra, int* rb);
 
-/* Pins the plan ra x rb (one of the candidates for n) for pass kind 0 (x) or
- * 1 (y/z) in this process.  ES_ERR_SIZE if it is not a candidate. */
+/* Pins the plan (ra, rb) (one of the candidates for n, named as above) for
+ * pass kind 0 (x) or 1 (y/z) in this process.  ES_ERR_SIZE if it is not a
+ * candidate. */
 int es_fft_plan_select(int pass_kind, int n, int ra, int rb);
 
 /* Device time [ms] of each kernel of the last time step of the last es_run

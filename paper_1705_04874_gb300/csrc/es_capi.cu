@@ -818,6 +818,8 @@ int run_checked_args(es_model* m, int nt, double dt, int n_rcv)
     return ES_OK;
 }
 
+bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
+
 // One staggered derivative of a plain [nz][ny][nx] array along `axis`, with
 // its own tables: out = D f (acc == nullptr) or out += acc * D f (acc: a
 // per-cell coefficient array, e.g. ones).  Stream-ordered; tables freed after
@@ -1666,6 +1668,7 @@ int es_derivative(const float* f, int nx, int ny, int nz, int axis, double d, in
 {
     if (!f || !out || f == out || axis < 0 || axis > 2 || !(d > 0) || (shift != 1 && shift != -1)) return ES_ERR_ARG;
     if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return ES_ERR_SIZE;
+    if (!aligned16(f) || !aligned16(out)) return ES_ERR_ARG;  // the passes move 8- and 16-byte vectors
     if (!is_device_ptr(f) || !is_device_ptr(out)) return ES_ERR_ARG;
     cudaGetLastError();
     int rc = ensure_prepared();
@@ -1681,15 +1684,17 @@ int es_laplacian(const float* f, int nx, int ny, int nz, double dx, double dy, d
 {
     if (!f || !out || f == out || !(dx > 0) || !(dy > 0) || !(dz > 0)) return ES_ERR_ARG;
     if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return ES_ERR_SIZE;
+    if (!aligned16(f) || !aligned16(out)) return ES_ERR_ARG;
     if (!is_device_ptr(f) || !is_device_ptr(out)) return ES_ERR_ARG;
     cudaGetLastError();
     int rc = ensure_prepared();
     if (rc != ES_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny * nz;
+    const size_t n_al = (n + 63) / 64 * 64;  // the second array on a 256-byte boundary
     float* tmp = nullptr;
-    CK(dev_alloc(&tmp, 2 * n * sizeof(float)));
-    float* ones = tmp + n;
+    CK(dev_alloc(&tmp, (n_al + n) * sizeof(float)));
+    float* ones = tmp + n_al;
     const double d[3] = {dx, dy, dz};
     cudaError_t e = launch_fill(ones, n, 1.f, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, n * sizeof(float), st);

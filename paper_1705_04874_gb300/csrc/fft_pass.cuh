@@ -305,9 +305,10 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
 }
 
 // Epilogue for 4 x-consecutive cells of one x line (x pass): q0 = linear
-// index of the first, pos0 its x, d[] the derivatives.
+// index of the first, pos0 its x, line = y + ny z (the x slabs' row index),
+// d[] the derivatives.
 __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob& J, size_t q0, int pos0,
-                                              int y, int z, const float* d, size_t off, size_t soff)
+                                              int line, const float* d, size_t off, size_t soff)
 {
     if (J.kind == JOB_STORE) {
         *reinterpret_cast<float4*>(J.tgt[0] + off + q0) = make_float4(d[0], d[1], d[2], d[3]);
@@ -315,7 +316,7 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
     }
     const float dt = p.dt;
     const int S = 2 * p.L + 1;
-    const size_t srow = soff + (size_t)S * ((size_t)y + (size_t)p.ny * z);
+    const size_t srow = soff + (size_t)S * (size_t)line;  // slab_index(0, ...) without the division
     if (J.kind == JOB_SINGLE) {
         const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -894,18 +895,20 @@ pass_strided(const __grid_constant__ PassParams p)
 // global memory (L1 / L2: the CTA read the whole tile at its start), then the
 // field update, four consecutive x of one line per item.  OFS = first tap
 // offset.
-template <int N, int CPAD, int OFS>
+template <int N, int CPAD, int OFS, int NT>
 __device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJob& J, const float* bf,
                                                 const float* src, int line0, int nlines, size_t off, size_t soff)
 {
     constexpr int LINES = 2 * CP;
     constexpr int ITEMS = LINES * N / 4;
+
     // x = xx - 8 .. xx + 11 in five float4 chunks (wrapped along the line); the
     // taps of the four outputs reach xx + OFS .. xx + 3 + OFS + NEAR_TAPS - 1
     static_assert(8 + OFS >= 0 && 8 + 3 + OFS + NEAR_TAPS - 1 < 20, "near taps outside the window");
-    const int nthreads = blockDim.x;
 #pragma unroll 2
-    for (int it = threadIdx.x; it < ITEMS; it += nthreads) {
+    for (int i = 0; i < (ITEMS + NT - 1) / NT; ++i) {
+        const int it = (int)threadIdx.x + i * NT;
+        if (ITEMS % NT != 0 && it >= ITEMS) break;
         const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
         const int xx = (hi * 4 + lo) * 4;
         const int line = line0 + r;
@@ -934,7 +937,7 @@ __device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJ
         float d[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) d[e] = __fadd_rn(bf[((xx + e) * CPAD) * 2 + r], sn[e]);
-        epilogue_quad(p, J, (size_t)line * N + xx, xx, line % p.ny, line / p.ny, d, off, soff);
+        epilogue_quad(p, J, (size_t)line * N + xx, xx, line, d, off, soff);
     }
 }
 
@@ -1046,9 +1049,16 @@ __device__ __forceinline__ void pass_x_epilogue_any(const PassParams& p, const P
     }
     __syncthreads();
     const size_t q0 = (size_t)line0 * N;
-    // 16-byte chunks need a 16-byte aligned simulation offset too (an odd cell
-    // count per simulation leaves every other one unaligned)
-    const int nq = (off & 3) == 0 ? nf / 4 : 0;
+    // 16-byte chunks need every array they touch on a 16-byte boundary at the
+    // tile (the tile's own offset q0 is a multiple of 4 cells): the targets
+    // at this simulation's offset (an odd cell count per simulation leaves
+    // every other one unaligned) and the coefficient arrays, which a caller
+    // may pass at any 4-byte offset
+    auto a16 = [](const float* q) { return ((uintptr_t)q & 15) == 0; };
+    bool vec = a16(J.tgt[0] + off);
+    if (J.kind == JOB_NORMAL) vec = vec && a16(J.tgt[1] + off) && a16(J.tgt[2] + off) && a16(J.coef[1]);
+    if (J.kind != JOB_STORE) vec = vec && a16(J.coef[0]);
+    const int nq = vec ? nf / 4 : 0;
     for (int i = tid; i < nq; i += NT)
         epilogue_quad_flat<N>(p, J, q0 + 4 * (size_t)i, 4 * i, line0, reinterpret_cast<const float4*>(bf)[i], off,
                               soff);
@@ -1101,7 +1111,9 @@ pass_x(const __grid_constant__ PassParams p)
     }
     if constexpr (N % 16 == 0) {
 #pragma unroll
-        for (int it = tid; it < ITEMS; it += NT) {
+        for (int i = 0; i < (ITEMS + NT - 1) / NT; ++i) {
+            const int it = tid + i * NT;
+            if (ITEMS % NT != 0 && it >= ITEMS) break;
             const int lo = it & 3, r = (it >> 2) & (LINES - 1), hi = it >> 7;
             const int xx = (hi * 4 + lo) * 4;
             const int line = line0 + r;
@@ -1153,8 +1165,8 @@ pass_x(const __grid_constant__ PassParams p)
     __syncthreads();
     if (p.pdl == 1) pdl_wait();  // the previous pass's updates of the targets come first
     if constexpr (N % 16 == 0) {
-        if (J.sign > 0) pass_x_epilogue<N, CPAD, near_ofs(+1)>(p, J, bf, src, line0, nlines, off, soff);
-        else pass_x_epilogue<N, CPAD, near_ofs(-1)>(p, J, bf, src, line0, nlines, off, soff);
+        if (J.sign > 0) pass_x_epilogue<N, CPAD, near_ofs(+1), NT>(p, J, bf, src, line0, nlines, off, soff);
+        else pass_x_epilogue<N, CPAD, near_ofs(-1), NT>(p, J, bf, src, line0, nlines, off, soff);
     } else {
         const float* srcs = reinterpret_cast<const float*>(s_hm + N);
         if (J.sign > 0) pass_x_epilogue_any<N, CPAD, near_ofs(+1), NT>(p, J, bf, srcs, line0, nlines, off, soff);

@@ -126,3 +126,15 @@ def test_fft_plan_table_without_a_gpu(lib):
                 assert (ra.value, rb.value) == c
             assert lib.es_fft_plan_select(kind, n, n, 1) == es.ES_ERR_SIZE
     assert lib.es_fft_plan_select(2, 64, 8, 8) == es.ES_ERR_ARG
+
+
+def test_derivative_entry_points_check_alignment_without_a_gpu(lib):
+    """es_derivative and es_laplacian refuse input or output arrays off a
+    16-byte boundary (the passes move 8- and 16-byte vectors) before touching
+    a device."""
+    from paper_1705_04874_gb300 import es
+    p, q = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20004)
+    assert lib.es_derivative(p, 32, 32, 32, 0, ctypes.c_double(10.0), 1, q, None) == es.ES_ERR_ARG
+    assert lib.es_derivative(q, 32, 32, 32, 0, ctypes.c_double(10.0), 1, p, None) == es.ES_ERR_ARG
+    assert lib.es_laplacian(p, 32, 32, 32, ctypes.c_double(10.0), ctypes.c_double(10.0), ctypes.c_double(10.0),
+                            q, None) == es.ES_ERR_ARG
