@@ -309,6 +309,16 @@ const char* es_last_error(void);
 void es_fault_inject_alloc(int n);
 long long es_debug_live_allocations(void);
 
+/* Bounds-checked debug build (libes_bounds.so, compiled with -DES_BOUNDS=1):
+ * the derivative passes check each global index of their loads, stores and
+ * reductions against its array's extent, skip an access out of range and
+ * record the first one.  es_debug_bounds reads and clears that record:
+ * *first_bad = 0 if every index was in range, else (source line << 40) |
+ * (the index's low 40 bits).  ES_ERR_STATE in the release build (which checks
+ * nothing), ES_ERR_ARG for a null pointer, ES_ERR_CUDA if the device word
+ * cannot be read. */
+int es_debug_bounds(long long* first_bad);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 """Builds libes.so (the CUDA solver behind include/es.h) in-tree with nvcc for
 sm_103a: one object per translation unit, compiled in parallel, then linked
-with the static CUDA runtime."""
+with the static CUDA runtime.  build(bounds=True) builds the bounds-checked
+debug library libes_bounds.so (-DES_BOUNDS=1) beside it."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libes.so")
+BOUNDS_OUT = os.path.join(HERE, "_build_bounds")
+BOUNDS_LIB = os.path.join(BOUNDS_OUT, "libes_bounds.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,23 +39,25 @@ def _deps():
         sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "es.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    out, lib = (BOUNDS_OUT, BOUNDS_LIB) if bounds else (OUT, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     exe = nvcc()
+    flags = FLAGS + (["-DES_BOUNDS=1"] if bounds else [])
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(out, os.path.basename(src).replace(".cu", ".o"))
+        cmd = [exe, *ARCH, *flags, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -65,16 +70,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose and log:
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp, "-lcudart_static", "-lrt",
            "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv))

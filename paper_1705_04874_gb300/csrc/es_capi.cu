@@ -207,6 +207,7 @@ int ensure_prepared()
         load_plan_cache();
         g_prepared_dev = dev;
     }
+    if (!bounds_init()) return cuda_fail(cudaErrorMemoryAllocation, "bounds word");
     return ES_OK;
 }
 
@@ -358,6 +359,7 @@ struct es_model {
     size_t sp_cap = 0;
     const int* sp_off[3] = {};
     const SpecialCell* sp_cells[3] = {};
+    int sp_n[3] = {};  // entries of each list
     cudaEvent_t ev[2 * KPS_MAX] = {};
     float last_ms[KPS_MAX] = {};
     int n_last = 0;
@@ -554,6 +556,7 @@ int build_special(es_model* m, const std::vector<long long>& rcv_cells)
     }
     char* cur = m->d_sp;
     for (int k = 0; k < 3; ++k) {
+        m->sp_n[k] = (int)cells[k].size();
         m->sp_cells[k] = reinterpret_cast<const SpecialCell*>(cur);
         if (!cells[k].empty())
             CK(cudaMemcpyAsync(cur, cells[k].data(), cells[k].size() * sizeof(SpecialCell), cudaMemcpyHostToDevice,
@@ -595,6 +598,10 @@ PassParams make_pass(const es_model* m, int axis, bool stress, float dt)
     p.nsim = m->nsim;
     p.fstride = (long long)m->ncell;
     p.sstride = (long long)slab_count(m, axis);
+    p.ext_f = p.fstride * m->nsim;
+    p.ext_s = p.sstride * m->nsim;
+    p.ext_c = p.fstride;
+    p.bad = bounds_word();
     auto taps = [&](PassJob& J) {
         for (int t = 0; t < NEAR_TAPS; ++t) J.g[t] = J.sign > 0 ? m->gp[axis][t] : m->gm[axis][t];
     };
@@ -667,6 +674,8 @@ int enqueue_step(es_model* m, float dt, int n_rcv, long long start, cudaStream_t
         p.rec = m->d_rec;
         p.rec_start = start;
         p.n_rcv = n_rcv;
+        p.ext_sp = m->sp_n[mode - 1];
+        p.ext_rec = (long long)m->rec_cap;
     };
     for (int a = 0; a < 3; ++a) {
         NvtxRange r(kVel[a]);
@@ -820,6 +829,34 @@ int run_checked_args(es_model* m, int nt, double dt, int n_rcv)
 
 bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
 
+}  // namespace
+
+// The device word of the bounds-checked build, allocated (outside the counted
+// allocations: it lives as long as the process) by ensure_prepared, which
+// every entry point calls before it launches or captures anything.
+namespace es {
+#if ES_BOUNDS
+static unsigned long long* g_bounds_word = nullptr;
+bool bounds_init()
+{
+    if (!g_bounds_word) {
+        if (cudaMalloc(&g_bounds_word, sizeof(unsigned long long)) != cudaSuccess) {
+            g_bounds_word = nullptr;
+            return false;
+        }
+        if (cudaMemset(g_bounds_word, 0, sizeof(unsigned long long)) != cudaSuccess) return false;
+    }
+    return true;
+}
+unsigned long long* bounds_word() { return g_bounds_word; }
+#else
+bool bounds_init() { return true; }
+unsigned long long* bounds_word() { return nullptr; }
+#endif
+}  // namespace es
+
+namespace {
+
 // One staggered derivative of a plain [nz][ny][nx] array along `axis`, with
 // its own tables: out = D f (acc == nullptr) or out += acc * D f (acc: a
 // per-cell coefficient array, e.g. ones).  Stream-ordered; tables freed after
@@ -860,6 +897,8 @@ cudaError_t derivative_pass(const float* f, int nx, int ny, int nz, int axis, do
         p.ckp = ck;
         p.ckm = ck + n;
         p.circ = circ ? 1 : 0;
+        p.ext_f = p.ext_c = (long long)nx * ny * nz;
+        p.bad = bounds_word();
         p.job[0].src = f;
         p.job[0].tgt[0] = out;
         p.job[0].kind = acc ? JOB_SINGLE : JOB_STORE;
@@ -897,6 +936,25 @@ const char* es_last_error(void) { return g_err; }
 void es_fault_inject_alloc(int n) { g_alloc_countdown = n > 0 ? n : 0; }
 
 long long es_debug_live_allocations(void) { return g_live_allocs.load(); }
+
+int es_debug_bounds(long long* first_bad)
+{
+    if (!first_bad) return ES_ERR_ARG;
+    *first_bad = 0;
+#if ES_BOUNDS
+    const int rc = ensure_prepared();
+    if (rc != ES_OK) return rc;
+    unsigned long long* w = bounds_word();
+    unsigned long long v = 0;
+    if (!w || cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(w, 0, sizeof v) != cudaSuccess)
+        return ES_ERR_CUDA;
+    *first_bad = (long long)v;
+    return ES_OK;
+#else
+    return ES_ERR_STATE;
+#endif
+}
 
 void es_model_destroy(es_model* m)
 {

@@ -110,7 +110,28 @@ struct PassParams {
     float* rec;
     long long rec_start;
     int n_rcv;
+    // Extents for the bounds-checked build (ES_BOUNDS): elements of each field
+    // array (all simulations), of each slab array of this axis, of each
+    // coefficient array, of the receiver buffer, and entries of sp; bad: where
+    // that build records the first index out of range (null otherwise).
+    long long ext_f, ext_s, ext_c, ext_rec;
+    int ext_sp;
+    unsigned long long* bad;
 };
+
+// Bounds-checked debug build: compiled with -DES_BOUNDS=1 (libes_bounds.so),
+// the pass kernels check each global index of their loads, stores and
+// reductions against the array's extent before the access; an index out of
+// range is recorded in *PassParams::bad (the first one: source line << 40 |
+// the index's low 40 bits) and the access skipped, so the kernel never leaves
+// its arrays.  The release build compiles the checks to nothing.
+#ifndef ES_BOUNDS
+#define ES_BOUNDS 0
+#endif
+// the device word of the bounds-checked build (null in the release build),
+// and its allocation (a no-op in the release build; false if it failed)
+unsigned long long* bounds_word();
+bool bounds_init();
 
 // Plan of the FFT for an axis length, as (R1, n / R1) (0 if unsupported).
 int plan_radices(int n, int* ra, int* rb);

@@ -118,6 +118,25 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return d;
 }
+// Index check of the bounds-checked build (ES_BOUNDS, es_internal.h): true
+// when 0 <= i < n; otherwise the first such index is recorded with the source
+// line and the caller skips the access.  Always true in the release build.
+__device__ __forceinline__ bool inb(unsigned long long* bad, long long i, long long n, int line)
+{
+#if ES_BOUNDS
+    if (i >= 0 && i < n) return true;
+    if (bad) atomicCAS(bad, 0ull, ((unsigned long long)line << 40) | ((unsigned long long)i & 0xFFFFFFFFFFull));
+    return false;
+#else
+    (void)bad;
+    (void)i;
+    (void)n;
+    (void)line;
+    return true;
+#endif
+}
+#define ES_INB(p, i, n) inb((p).bad, (long long)(i), (long long)(n), __LINE__)
+
 __device__ __forceinline__ float2 add2(float2 a, float2 b)
 {
     float2 d;
@@ -269,10 +288,12 @@ __device__ __forceinline__ float normal_coef(float lam, float mu, bool diag) { r
 __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob& J, size_t q, int pos,
                                               int x, int y, int z, float d0, float d1, size_t off, size_t soff)
 {
+    if (!ES_INB(p, off + q + 1, p.ext_f)) return;
     if (J.kind == JOB_STORE) {
         *reinterpret_cast<float2*>(J.tgt[0] + off + q) = make_float2(d0, d1);
         return;
     }
+    if (!ES_INB(p, q + 1, p.ext_c)) return;
     const float dt = p.dt;
     const bool slab = in_slab(pos, p.n, p.L);
     const int S = 2 * p.L + 1;
@@ -282,6 +303,7 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
         if (slab) {
             const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
             const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            if (!ES_INB(p, soff + si + 1, p.ext_s)) return;
             inc.x = split_delta(J.slab[0], soff + si, P, inc.x);
             inc.y = split_delta(J.slab[0], soff + si + 1, P, inc.y);
         }
@@ -291,6 +313,7 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
         const float2 mu = __ldg(reinterpret_cast<const float2*>(J.coef[1] + q));
         const float P = slab ? __ldg(p.pc + pos) : 1.f;
         const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+        if (slab && !ES_INB(p, soff + si + 1, p.ext_s)) return;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const float2 c = make_float2(normal_coef(lam.x, mu.x, t == J.diag), normal_coef(lam.y, mu.y, t == J.diag));
@@ -310,10 +333,14 @@ __device__ __forceinline__ void epilogue_pair(const PassParams& p, const PassJob
 __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob& J, size_t q0, int pos0,
                                               int line, const float* d, size_t off, size_t soff)
 {
+    if (!ES_INB(p, off + q0 + 3, p.ext_f)) return;
     if (J.kind == JOB_STORE) {
         *reinterpret_cast<float4*>(J.tgt[0] + off + q0) = make_float4(d[0], d[1], d[2], d[3]);
         return;
     }
+    // the coefficients, and this line's row of the x slabs (S cells)
+    if (!ES_INB(p, q0 + 3, p.ext_c)) return;
+    if (p.L > 0 && !ES_INB(p, soff + (size_t)(2 * p.L + 1) * (line + 1) - 1, p.ext_s)) return;
     const float dt = p.dt;
     const int S = 2 * p.L + 1;
     const size_t srow = soff + (size_t)S * (size_t)line;  // slab_index(0, ...) without the division
@@ -356,10 +383,12 @@ __device__ __forceinline__ void epilogue_quad(const PassParams& p, const PassJob
 __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob& J, size_t q, int pos, int x, int y,
                                              int z, float d, size_t off, size_t soff)
 {
+    if (!ES_INB(p, off + q, p.ext_f)) return;
     if (J.kind == JOB_STORE) {
         J.tgt[0][off + q] = d;
         return;
     }
+    if (!ES_INB(p, q, p.ext_c)) return;
     const float dt = p.dt;
     const bool slab = in_slab(pos, p.n, p.L);
     const int S = 2 * p.L + 1;
@@ -368,6 +397,7 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
         if (slab) {
             const float P = __ldg((J.stag ? p.ps : p.pc) + pos);
             const size_t si = slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S);
+            if (!ES_INB(p, soff + si, p.ext_s)) return;
             inc = split_delta(J.slab[0], soff + si, P, inc);
         }
         atomicAdd(J.tgt[0] + off + q, inc);
@@ -375,6 +405,7 @@ __device__ __forceinline__ void epilogue_one(const PassParams& p, const PassJob&
         const float lam = __ldg(J.coef[0] + q), mu = __ldg(J.coef[1] + q);
         const float P = slab ? __ldg(p.pc + pos) : 1.f;
         const size_t si = slab ? slab_index(p.axis, x, y, z, slab_pos(pos, p.n, p.L), p.nx, p.ny, S) : 0;
+        if (slab && !ES_INB(p, soff + si, p.ext_s)) return;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             float inc = increment(dt, normal_coef(lam, mu, t == J.diag), d);
@@ -704,13 +735,14 @@ __device__ __forceinline__ void special_phase(const PassParams& p, const PassJob
         if (threadIdx.x == 0) {
             if (p.pdl == 1) pdl_wait();  // (done already if this thread had cells to update)
             for (int e = b0; e < b1; ++e) {
+                if (!ES_INB(p, e, p.ext_sp)) break;
                 const SpecialCell c = p.sp[e];
                 if (c.kind == SP_RECEIVER) break;
                 const SourceDev& s = p.src[c.idx];
                 if (n >= s.nw) continue;
                 const float w = s.w[n];
                 auto add = [&](float* t, float m) {
-                    if (m != 0.f) *t = __fmaf_rn(m, w, __ldcg(t));
+                    if (m != 0.f && ES_INB(p, c.q, p.ext_f)) *t = __fmaf_rn(m, w, __ldcg(t));
                 };
                 if (p.sp_mode == SP_VEL_Z) {
                     if (c.kind == SP_FORCE) add(J.tgt[0] + c.q, s.m[job]);
@@ -732,9 +764,12 @@ __device__ __forceinline__ void special_phase(const PassParams& p, const PassJob
     if (p.sp_mode == SP_STR_Y || (p.sp_mode == SP_STR_Z && job != 0)) return;
     if (p.pdl == 1) pdl_wait();
     for (int e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+        if (!ES_INB(p, e, p.ext_sp)) break;
         const SpecialCell c = p.sp[e];
         if (c.kind != SP_RECEIVER) continue;
-        float* row = p.rec + ((size_t)(n - p.rec_start) * p.nsim + c.sim) * 4 * p.n_rcv;
+        const size_t row0 = ((size_t)(n - p.rec_start) * p.nsim + c.sim) * 4 * p.n_rcv;
+        if (!ES_INB(p, c.q, p.ext_f) || !ES_INB(p, row0 + 4 * (size_t)p.n_rcv - 1, p.ext_rec)) continue;
+        float* row = p.rec + row0;
         if (p.sp_mode == SP_VEL_Z) {
             row[(size_t)(job + 1) * p.n_rcv + c.idx] = __ldcg(J.tgt[0] + c.q);
         } else {
@@ -807,20 +842,23 @@ pass_strided(const __grid_constant__ PassParams p)
 #pragma unroll
         for (int r = 0; r < RA; ++r) {
             const float* g = src + (size_t)(j + r * BA) * est;
-            a[r].x = valid ? __ldg(g) : 0.f;
-            a[r].y = valid1 ? __ldg(g + 1) : 0.f;
+            a[r].x = valid && ES_INB(p, off + base + (size_t)(j + r * BA) * est, p.ext_f) ? __ldg(g) : 0.f;
+            a[r].y = valid1 && ES_INB(p, off + base + (size_t)(j + r * BA) * est + 1, p.ext_f) ? __ldg(g + 1) : 0.f;
         }
     } else {
 #pragma unroll
         for (int r = 0; r < RA; ++r)
-            a[r] = valid ? __ldg(reinterpret_cast<const float2*>(src + (size_t)(j + r * BA) * est))
-                         : make_float2(0.f, 0.f);
+            a[r] = valid && ES_INB(p, off + base + (size_t)(j + r * BA) * est + 1, p.ext_f)
+                       ? __ldg(reinterpret_cast<const float2*>(src + (size_t)(j + r * BA) * est))
+                       : make_float2(0.f, 0.f);
     }
     // coefficient rows of this tile (128 bytes each) into L2 for the epilogue
     if (tid < N && J.coef[0] && tx * 2 * CP < p.nx) {
         const size_t row = base - 2 * c + (size_t)tid * est;
-        prefetch_l2(J.coef[0] + row);
-        if (J.coef[1]) prefetch_l2(J.coef[1] + row);
+        if (ES_INB(p, row, p.ext_c)) {
+            prefetch_l2(J.coef[0] + row);
+            if (J.coef[1]) prefetch_l2(J.coef[1] + row);
+        }
     }
     load_tables<N>(p, s_tw, s_hp, s_hm, tid, T * CP);
     Dft<RA>::run(a);
@@ -836,6 +874,12 @@ pass_strided(const __grid_constant__ PassParams p)
         const size_t gstep = (size_t)BA * est;
 #pragma unroll 1
         for (int r = 0; r < RA; ++r, g += gstep, sb += BA * CP) {
+#if ES_BOUNDS
+            if (!ES_INB(p, off + base + (size_t)(j + r * BA) * est + (ODD && !valid1 ? 0 : 1), p.ext_f)) {
+                *sb = make_float2(0.f, 0.f);
+                continue;
+            }
+#endif
             if constexpr (ODD) {
                 cp_async4(&sb->x, g);
                 if (valid1) cp_async4(&sb->y, g + 1);
@@ -852,6 +896,12 @@ pass_strided(const __grid_constant__ PassParams p)
         const int pos = h < HALO ? N - HALO + h : h - HALO;
         float2* d = buf + (h < HALO ? h : N + h) * CP + cc;
         const float* g = J.src + off + base - 2 * c + 2 * cc + (size_t)pos * est;
+#if ES_BOUNDS
+        if (!ES_INB(p, off + base - 2 * c + 2 * cc + (size_t)pos * est + (ODD && xc + 1 >= p.nx ? 0 : 1), p.ext_f)) {
+            *d = make_float2(0.f, 0.f);
+            continue;
+        }
+#endif
         if constexpr (ODD) {
             cp_async4(&d->x, g);
             if (xc + 1 < p.nx) cp_async4(&d->y, g + 1);
@@ -919,6 +969,9 @@ __device__ __forceinline__ void pass_x_epilogue(const PassParams& p, const PassJ
         for (int m = 0; m < 5; ++m) {
             const int x0 = (xx - 8 + 4 * m + N) % N;
             if (4 * m + 3 < 8 + OFS || 4 * m > 8 + 3 + OFS + NEAR_TAPS - 1) continue;  // chunk unused
+#if ES_BOUNDS
+            if (!ES_INB(p, off + (size_t)line * N + x0 + 3, p.ext_f)) return;
+#endif
             const float4 v = __ldg(reinterpret_cast<const float4*>(ln + x0));
             w[4 * m] = v.x;
             w[4 * m + 1] = v.y;
@@ -949,10 +1002,12 @@ template <int N>
 __device__ __forceinline__ void epilogue_quad_flat(const PassParams& p, const PassJob& J, size_t q0, int f0,
                                                    int line0, float4 d4, size_t off, size_t soff)
 {
+    if (!ES_INB(p, off + q0 + 3, p.ext_f)) return;
     if (J.kind == JOB_STORE) {
         *reinterpret_cast<float4*>(J.tgt[0] + off + q0) = d4;
         return;
     }
+    if (!ES_INB(p, q0 + 3, p.ext_c)) return;
     const float d[4] = {d4.x, d4.y, d4.z, d4.w};
     const float dt = p.dt;
     const int S = 2 * p.L + 1;
@@ -963,6 +1018,7 @@ __device__ __forceinline__ void epilogue_quad_flat(const PassParams& p, const Pa
         const int r = (f0 + e) / N;
         xs[e] = f0 + e - r * N;
         srow[e] = soff + (size_t)S * (size_t)(line0 + r);
+        if (p.L > 0 && !ES_INB(p, srow[e] + S - 1, p.ext_s)) return;
     }
     if (J.kind == JOB_SINGLE) {
         const float4 c4 = __ldg(reinterpret_cast<const float4*>(J.coef[0] + q0));
@@ -1118,7 +1174,8 @@ pass_x(const __grid_constant__ PassParams p)
             const int xx = (hi * 4 + lo) * 4;
             const int line = line0 + r;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (line < nlines) v = __ldg(reinterpret_cast<const float4*>(src + (size_t)line * N + xx));
+            if (line < nlines && ES_INB(p, off + (size_t)line * N + xx + 3, p.ext_f))
+                v = __ldg(reinterpret_cast<const float4*>(src + (size_t)line * N + xx));
             bf[((xx + 0) * CPAD) * 2 + r] = v.x;
             bf[((xx + 1) * CPAD) * 2 + r] = v.y;
             bf[((xx + 2) * CPAD) * 2 + r] = v.z;
@@ -1138,7 +1195,7 @@ pass_x(const __grid_constant__ PassParams p)
             const int f = tid + i * NT;
             if (f < LINES * N) {
                 const int r = f / N, xx = f - r * N;
-                const float v = f < nf ? __ldg(tile + f) : 0.f;
+                const float v = f < nf && ES_INB(p, off + (size_t)line0 * N + f, p.ext_f) ? __ldg(tile + f) : 0.f;
                 bf[(xx * CPAD) * 2 + r] = v;
                 float* row = srcs + r * W + XHALO;
                 row[xx] = v;

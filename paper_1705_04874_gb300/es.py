@@ -37,15 +37,21 @@ class EsError(RuntimeError):
         self.status = status
 
 
+def bounds_build() -> bool:
+    """ES_BOUNDS=1 in the environment selects the bounds-checked debug build
+    (libes_bounds.so) for this process."""
+    return os.environ.get("ES_BOUNDS", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.BOUNDS_LIB if bounds_build() else _build.LIB
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(bounds=bounds_build())
             lib = ctypes.CDLL(path)
             c_int, c_double, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
             pi = ctypes.POINTER(ctypes.c_int)
@@ -85,6 +91,7 @@ def _load():
                 "es_last_error": ([], ctypes.c_char_p),
                 "es_fault_inject_alloc": ([c_int], None),
                 "es_debug_live_allocations": ([], ctypes.c_longlong),
+                "es_debug_bounds": ([ctypes.POINTER(ctypes.c_longlong)], c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -104,7 +111,7 @@ def exported_symbols():
             "es_fft_plan_select", "es_sur_create", "es_sur_destroy", "es_sur_set_stream", "es_sur_num_params",
             "es_sur_get_params", "es_sur_set_params", "es_sur_set_output_scale", "es_sur_fit_output_scale",
             "es_sur_predict", "es_sur_loss_grad", "es_sur_train_step", "es_sur_combine", "es_gemm_bf16", "es_gemm_status", "es_gemm_wait_probe", "es_model_destroy", "es_status_string", "es_last_error",
-            "es_fault_inject_alloc", "es_debug_live_allocations"]
+            "es_fault_inject_alloc", "es_debug_live_allocations", "es_debug_bounds"]
 
 
 def _check(status, where):
@@ -396,3 +403,11 @@ class Model:
 
     def kernels_per_step(self):
         return int(self._lib.es_kernels_per_step(self._h))
+
+
+def es_debug_bounds():
+    """First out-of-range index recorded by the bounds-checked build since the
+    last call (0: none), as (source line, index low 40 bits, raw value)."""
+    v = ctypes.c_longlong()
+    _check(_load().es_debug_bounds(ctypes.byref(v)), "es_debug_bounds")
+    return (v.value >> 40, v.value & ((1 << 40) - 1), v.value)

@@ -138,3 +138,13 @@ def test_derivative_entry_points_check_alignment_without_a_gpu(lib):
     assert lib.es_derivative(q, 32, 32, 32, 0, ctypes.c_double(10.0), 1, p, None) == es.ES_ERR_ARG
     assert lib.es_laplacian(p, 32, 32, 32, ctypes.c_double(10.0), ctypes.c_double(10.0), ctypes.c_double(10.0),
                             q, None) == es.ES_ERR_ARG
+
+
+def test_bounds_query_in_the_release_build(lib):
+    """The release library checks no indexes: es_debug_bounds answers
+    ES_ERR_STATE (ES_ERR_ARG for a null pointer) without touching a device."""
+    from paper_1705_04874_gb300 import es
+    v = ctypes.c_longlong(7)
+    assert lib.es_debug_bounds(None) == es.ES_ERR_ARG
+    assert lib.es_debug_bounds(ctypes.byref(v)) == es.ES_ERR_STATE
+    assert v.value == 0
