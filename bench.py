@@ -35,6 +35,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1705_04874_gb300 import synth  # noqa: E402
+
+PASS_SOURCE = os.path.join(ROOT, "paper_1705_04874_gb300", "csrc", "fft_pass.cuh")
+
+
+def kernel_code_hash(path: str = PASS_SOURCE) -> str:
+    """sha256 of the pass kernels' code with comments and blank lines removed
+    (the key under which profiles/traffic.json records its ncu DRAM bytes)."""
+    import hashlib
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()
 from paper_1705_04874_gb300.replicas import max_over_ranks, sum_over_ranks  # noqa: E402
 
 # algorithmic bytes per cell for one launch of each pass kernel (FP32), the
@@ -293,12 +307,10 @@ def main():
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
-        # ncu DRAM bytes per launch, valid only for the kernel source they were taken on
-        import hashlib
+        # ncu DRAM bytes per launch, valid only for the kernel code they were taken on
         try:
             rec = json.load(open(prof))
-            src = open(os.path.join(ROOT, "paper_1705_04874_gb300", "csrc", "fft_pass.cuh"), "rb").read()
-            if hashlib.sha256(src).hexdigest().startswith(rec.get("kernel_source_sha256_prefix", "-")):
+            if kernel_code_hash().startswith(rec.get("kernel_code_sha256_prefix", "-")):
                 traffic = rec.get(f"{args.workload}:{dom}")
         except (OSError, ValueError):
             traffic = None

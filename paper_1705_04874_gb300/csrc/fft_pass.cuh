@@ -18,20 +18,25 @@
 // multiply and that stage happen in registers; shared memory is touched only
 // between stages.  The inverse's last stage ends on the same elements the
 // first forward stage loaded, so the epilogue writes where the loads read.
+// Three-stage plans (Core3: 125 = 5 x 5 x 5, 75 = 3 x 5 x 5) run their middle
+// stages through shared memory and keep the same first / last-stage layout.
 //
 // Strided passes (y, z): a tile is 32 consecutive x (128-byte rows) by the
-// whole pencil; every global access of a warp is a full row segment.  The x
-// pass stages 32 whole x-lines (contiguous in memory) through shared memory
-// with float4 accesses (float accesses when the length is not a multiple of
-// 16) and runs the same FFT core on the staged tile.
+// whole pencil; every global access of a warp is a full row segment (an odd
+// nx moves the x-adjacent pairs as two floats).  The x pass stages 32 whole
+// x-lines (contiguous in memory) through shared memory with float4 accesses
+// (float accesses, and a per-line copy of the source for the near stencil,
+// when the length is not a multiple of 16) and runs the same FFT core on the
+// staged tile.
 //
 // Each derivative is evaluated as a near part plus a far part (es_internal.h):
 // the multiplier tables hold H_far / n, and once the last inverse stage has
 // read the shared buffer, the source tile comes back into it (cp.async from
 // L2, where the tile's first read left it, with wrap-around copies of the
 // first and last rows); the epilogue adds the NEAR_TAPS-point near stencil
-// from there (the x pass reads it from the staged lines' L1 / L2 copies).  In exact arithmetic the sum is
-// the spectral derivative itself; in FP32 the FFT's roundoff, which is spread
+// from there (the x pass reads it from the staged lines' L1 / L2 copies, or
+// from its per-line copy).  In exact arithmetic the sum is the spectral
+// derivative itself; in FP32 the FFT's roundoff, which is spread
 // over the whole pencil, is scaled down by |H_far| / |H| (about 1 %), so
 // far-away receivers no longer see the FP32 noise of the pencil's largest
 // values.

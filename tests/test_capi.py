@@ -148,3 +148,17 @@ def test_bounds_query_in_the_release_build(lib):
     assert lib.es_debug_bounds(None) == es.ES_ERR_ARG
     assert lib.es_debug_bounds(ctypes.byref(v)) == es.ES_ERR_STATE
     assert v.value == 0
+
+
+def test_traffic_record_matches_the_pass_kernels():
+    """profiles/traffic.json (ncu DRAM bytes per pass launch, which bench.py
+    reports as roofline.traffic) is keyed by the pass kernels' code; the
+    committed record is that of the committed kernels."""
+    import importlib.util
+    import json
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    assert bench.kernel_code_hash().startswith(rec["kernel_code_sha256_prefix"])
+    assert all(rec[f"256:{k}"] > 0 for k in ("vel-x", "vel-y", "vel-z", "str-x", "str-y", "str-z"))
